@@ -1,0 +1,138 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) thermal pseudopotential D3Q19 lattice Boltzmann step.
+ *
+ * Method: Biferale, Perlekar, Sbragaglia, Toschi, "Convection in multiphase flows using
+ * Lattice Boltzmann methods" (arXiv:1111.0905), "Algorithm" paragraph, Eqs. (6)-(9), with
+ * the boundary conditions of the Fig. 1 caption and of the text around Eq. (4), and the
+ * heat-flux diagnostic of Eqs. (4)-(5).
+ *
+ * Lattice (the paper names D3Q19 but fixes no ordering): l = 0 rest; 1..6 = (+-1,0,0),
+ * (0,+-1,0), (0,0,+-1); 7..10 = (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0); 11..14 = (1,0,1),
+ * (-1,0,-1),(1,0,-1),(-1,0,1); 15..18 = (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1). Opposite pairs
+ * (1,2),(3,4),...,(17,18). Weights 1/3, 1/18 (axis), 1/36 (diagonal).
+ *
+ * Grid: nx*ny*nz nodes, node index idx = x + nx*(y + ny*z) (x fastest). Periodic in x and
+ * y; halfway no-slip walls at z = -1/2 (temperature T_d) and z = nz - 1/2 (T_u).
+ * Field arrays are float64, nx*ny*nz long, in node-index order.
+ * Population arrays are float64 [19][nx*ny*nz] (structure of arrays, l slowest).
+ *
+ * Ownership: the caller owns every array it passes; the context owns all device state
+ * (two ping-pong population lattices f and g, diagnostics scratch). Device pointers must
+ * be valid on the context's device and ordered on its stream.
+ *
+ * Errors: every int-returning call returns LB_OK (0) or a negative LB_E* code. Nothing is
+ * printed, nothing exits, no device trap is used. lb_last_error() gives the context's last
+ * message (for LB_ECUDA the CUDA error string).
+ *
+ * Threading: a context is used by one host thread at a time. All calls are ordered on the
+ * context's CUDA stream; calls that return host data synchronise that stream.
+ */
+#ifndef THERMAL_LBM_LB_H
+#define THERMAL_LBM_LB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_OK 0
+#define LB_EINVAL (-1)    /* invalid argument or parameter (tau <= 1/2, size, null pointer) */
+#define LB_ENOMEM (-2)    /* device or host allocation failed */
+#define LB_ECUDA (-3)     /* a CUDA call or kernel launch failed; see lb_last_error */
+#define LB_ENONPHYS (-4)  /* health check found rho <= 0, T <= 0 or a NaN */
+#define LB_EIO (-5)       /* checkpoint file could not be written/read or failed its checksum */
+#define LB_EUNSUP (-6)    /* operation not supported for this precision/configuration */
+
+/* Storage/compute precision of the populations. */
+typedef enum {
+  LB_FP64 = 0,     /* float64 storage and compute */
+  LB_FP32 = 1,     /* float32 storage and compute */
+  LB_BF16_DEV = 2, /* bfloat16 storage of f_l - w_l rho0 and g_l - w_l rho0 T0, float32 compute */
+  LB_FP16_DEV = 3  /* float16 storage of the same deviations, float32 compute */
+} lb_precision;
+
+typedef struct {
+  int nx, ny, nz;         /* grid; each >= 1, nx*ny*nz < 2^31 */
+  double tau_nu;          /* f relaxation time, Eq. (6); > 1/2 */
+  double tau_kappa;       /* g relaxation time, Eq. (7); > 1/2 */
+  double G;               /* pseudopotential coupling of Eq. (9); bulk P = rho T + (G/2) e^{-2/rho} */
+  double kappa;           /* thermal conductivity, Eqs. (2)-(3); > 0 */
+  double c_v;             /* specific heat at constant volume, Eq. (3); > 0 (1 = default) */
+  double g_z;             /* signed gravity along z, Eq. (1) (negative = downward) */
+  double T_d, T_u;        /* bottom / top wall temperatures */
+  double rho0, T0;        /* reference state of the 16-bit deviation storage; <= 0: mean of init */
+  int precision;          /* lb_precision */
+  int nu_every;           /* > 0: accumulate Nu_mean every nu_every steps into the time average */
+  int check_every;        /* > 0: lb_step checks rho > 0, T > 0, no NaN every check_every steps */
+  int tile_y;             /* launch shape: CTA tile is 32 x tile_y (4, 8 or 16; 0 = default 8) */
+  int z_chunk;            /* launch shape: planes per CTA (0 = choose from the grid size) */
+} lb_params;
+
+typedef struct lb_ctx lb_ctx;  /* opaque */
+
+/* lb_init -- allocate a context and set the initial state f = f^eq(rho, 0, T), g = g^eq(rho, T, 0)
+ * ("Algorithm" paragraph: equilibria of Eqs. (6)-(7) at rest).
+ * rho_init, T_init: float64 fields (node-index order), host memory if init_on_device == 0,
+ * device memory otherwise; copied, not retained. cuda_stream: a cudaStream_t (NULL = the
+ * legacy default stream) on the current device; every later call is ordered on it.
+ * On success *out is the new context. Errors: LB_EINVAL (parameters, rho <= 0 or T <= 0 or
+ * non-finite input), LB_ENOMEM, LB_ECUDA. On error *out is NULL and nothing is leaked. */
+int lb_init(const lb_params* params, const double* rho_init, const double* T_init,
+            int init_on_device, void* cuda_stream, lb_ctx** out);
+
+/* lb_step -- advance nsteps time steps of Eqs. (6)-(7): per step one fused launch that pull-
+ * streams f and g (periodic x/y, bounce-back walls), takes the moments of Eq. (8), the force of
+ * Eq. (9) with psi = exp(-1/rho) plus gravity rho g_z z, the shifted velocity u' = (j + tau_nu F)/rho,
+ * the physical velocity u = (j + F/2)/rho and its divergence, and collides f (temperature in
+ * f^eq) and g (with the counter term -rho T div u / c_v). Asynchronous on the context's stream
+ * unless nu_every/check_every ask for host-visible checks. nsteps >= 0.
+ * Errors: LB_EINVAL, LB_ECUDA (launch), LB_ENONPHYS (health check failed; the state is kept). */
+int lb_step(lb_ctx* ctx, long long nsteps);
+
+/* lb_moments -- macroscopic fields of the current state (Eq. (8)): rho, the physical velocity
+ * u = (j + F/2)/rho and T = (sum_l g_l)/rho. Each output is float64 [nx*ny*nz]; host memory if
+ * on_device == 0 (the call synchronises), device memory otherwise. Any output may be NULL.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+int lb_moments(lb_ctx* ctx, double* rho, double* ux, double* uy, double* uz, double* T,
+               int on_device);
+
+/* lb_nusselt -- layer heat flux of Eq. (4) as a Nusselt number,
+ * Nu(z) = <rho U u_z - kappa dT/dz>_{x,y} / (kappa (T_d - T_u)/nz), U = c_v T + (G/4) e^{-2/rho}
+ * (Eq. (2)), dT/dz by central differences with wall ghosts 2 T_wall - T. Host outputs:
+ * *nu_mean = mean over z; nu_z (may be NULL) = nz values; *nu_time_avg (may be NULL) = mean of
+ * the Nu_mean samples accumulated by lb_step with nu_every > 0 (NaN if none).
+ * FP64 warp-shuffle reductions on the device; synchronises. Errors: LB_EINVAL, LB_ECUDA. */
+int lb_nusselt(lb_ctx* ctx, double* nu_mean, double* nu_z, double* nu_time_avg);
+
+/* lb_populations -- the current pre-collision state (f_l, g_l) as float64 [19][nx*ny*nz] each
+ * (Eqs. (6)-(7): populations after streaming). Host memory if on_device == 0. Either pointer
+ * may be NULL. Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+int lb_populations(lb_ctx* ctx, double* f, double* g, int on_device);
+
+/* lb_diagnostics -- health and conservation of the current state, on the host:
+ * out[0] = min rho, out[1] = min T, out[2] = count of non-finite rho/T/u, out[3] = total mass
+ * sum rho, out[4] = total sum rho T. FP64 reductions. Errors: LB_EINVAL, LB_ECUDA. */
+int lb_diagnostics(lb_ctx* ctx, double out[5]);
+
+/* lb_save / lb_load -- checkpoint of (parameters, step count, populations in their storage
+ * precision) to a raw binary file with a header and a 64-bit FNV-1a checksum of the payload.
+ * lb_load requires a context created with the same grid and precision and replaces its state.
+ * Errors: LB_EINVAL, LB_EIO (open/write/read failure, bad magic, mismatch, checksum), LB_ECUDA. */
+int lb_save(lb_ctx* ctx, const char* path);
+int lb_load(lb_ctx* ctx, const char* path);
+
+/* lb_step_count -- number of steps taken since lb_init (or restored by lb_load); -1 if ctx is NULL. */
+long long lb_step_count(const lb_ctx* ctx);
+
+/* lb_free -- release the context and its device memory (synchronises its stream). NULL is a no-op. */
+void lb_free(lb_ctx* ctx);
+
+/* lb_strerror -- static description of an LB_E* code. */
+const char* lb_strerror(int code);
+
+/* lb_last_error -- the context's last error message ("" if none); a static message if ctx is NULL. */
+const char* lb_last_error(const lb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THERMAL_LBM_LB_H */

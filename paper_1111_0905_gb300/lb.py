@@ -1,0 +1,255 @@
+"""Python binding of the C ABI in include/lb.h (ctypes; argument marshalling only).
+
+Every step of the method runs in the sm_103a kernels of libthermal_lbm.so. PyTorch is used
+only for device memory (CUDA tensors whose pointers are passed through) and for the current
+CUDA stream. There is no CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field, fields
+from pathlib import Path
+
+import numpy as np
+
+LB_FP64, LB_FP32, LB_BF16_DEV, LB_FP16_DEV = 0, 1, 2, 3
+PRECISIONS = {"f64": LB_FP64, "f32": LB_FP32, "bf16dev": LB_BF16_DEV, "fp16dev": LB_FP16_DEV}
+STORAGE_BYTES = {LB_FP64: 8, LB_FP32: 4, LB_BF16_DEV: 2, LB_FP16_DEV: 2}
+Q = 19
+
+_LIB_PATH = Path(__file__).resolve().parent / "libthermal_lbm.so"
+_lib = None
+
+# Names declared in include/lb.h.
+EXPORTS = ("lb_init", "lb_step", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
+           "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error")
+
+
+class LbParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("tau_nu", ctypes.c_double), ("tau_kappa", ctypes.c_double), ("G", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("c_v", ctypes.c_double), ("g_z", ctypes.c_double),
+        ("T_d", ctypes.c_double), ("T_u", ctypes.c_double),
+        ("rho0", ctypes.c_double), ("T0", ctypes.c_double),
+        ("precision", ctypes.c_int), ("nu_every", ctypes.c_int), ("check_every", ctypes.c_int),
+        ("tile_y", ctypes.c_int), ("z_chunk", ctypes.c_int),
+    ]
+
+
+@dataclass
+class Params:
+    """Mirror of lb_params (include/lb.h)."""
+    nx: int
+    ny: int
+    nz: int
+    tau_nu: float
+    tau_kappa: float
+    G: float
+    kappa: float
+    c_v: float = 1.0
+    g_z: float = 0.0
+    T_d: float = 1.0 / 3.0
+    T_u: float = 1.0 / 3.0
+    rho0: float = 0.0
+    T0: float = 0.0
+    precision: int = LB_FP64
+    nu_every: int = 0
+    check_every: int = 0
+    tile_y: int = 0
+    z_chunk: int = 0
+
+    def to_c(self) -> LbParams:
+        return LbParams(*[getattr(self, f.name) for f in fields(self)])
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libthermal_lbm.so (built by paper_1111_0905_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_1111_0905_gb300.build.build()")
+    lib = ctypes.CDLL(str(_LIB_PATH))
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    DP = ctypes.POINTER(ctypes.c_double)
+    lib.lb_init.argtypes = [ctypes.POINTER(LbParams), P, P, I, P, ctypes.POINTER(P)]
+    lib.lb_init.restype = I
+    lib.lb_step.argtypes = [P, LL]
+    lib.lb_step.restype = I
+    lib.lb_moments.argtypes = [P, P, P, P, P, P, I]
+    lib.lb_moments.restype = I
+    lib.lb_nusselt.argtypes = [P, DP, P, DP]
+    lib.lb_nusselt.restype = I
+    lib.lb_populations.argtypes = [P, P, P, I]
+    lib.lb_populations.restype = I
+    lib.lb_diagnostics.argtypes = [P, P]
+    lib.lb_diagnostics.restype = I
+    lib.lb_save.argtypes = [P, ctypes.c_char_p]
+    lib.lb_save.restype = I
+    lib.lb_load.argtypes = [P, ctypes.c_char_p]
+    lib.lb_load.restype = I
+    lib.lb_step_count.argtypes = [P]
+    lib.lb_step_count.restype = LL
+    lib.lb_free.argtypes = [P]
+    lib.lb_free.restype = None
+    lib.lb_strerror.argtypes = [I]
+    lib.lb_strerror.restype = ctypes.c_char_p
+    lib.lb_last_error.argtypes = [P]
+    lib.lb_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _host_f64(a, n: int) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"field has {a.size} entries, grid has {n}")
+    return a
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:  # pragma: no cover
+        pass
+    return None
+
+
+class Lattice:
+    """A context of the C ABI: lb_init on construction, lb_free on close()."""
+
+    def __init__(self, params: Params, rho, T, stream=None):
+        self.lib = load_library()
+        self.params = params
+        self.shape = (params.nz, params.ny, params.nx)
+        self._ctx = ctypes.c_void_p()
+        n = params.N
+        on_device = not isinstance(rho, np.ndarray)
+        if on_device:
+            import torch
+            rho = rho.to(torch.float64).contiguous()
+            T = T.to(torch.float64).contiguous()
+            if rho.numel() != n or T.numel() != n:
+                raise ValueError("field size does not match the grid")
+            self._keep = (rho, T)
+        else:
+            rho, T = _host_f64(rho, n), _host_f64(T, n)
+        self.stream = _current_stream() if stream is None else stream
+        cp = params.to_c()
+        rc = self.lib.lb_init(ctypes.byref(cp), _ptr(rho), _ptr(T), int(on_device), self.stream,
+                              ctypes.byref(self._ctx))
+        if rc != 0:
+            raise LBError(rc, "lb_init", self.lib.lb_strerror(rc).decode())
+        self._keep = None
+
+    # -- helpers ----------------------------------------------------------------------------
+    def _check(self, rc: int, where: str):
+        if rc != 0:
+            msg = self.lib.lb_last_error(self._ctx).decode() or self.lib.lb_strerror(rc).decode()
+            raise LBError(rc, where, msg)
+
+    @property
+    def ctx(self):
+        if not self._ctx:
+            raise RuntimeError("lattice is closed")
+        return self._ctx
+
+    # -- C ABI ------------------------------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(self.lib.lb_step(self.ctx, int(n)), "lb_step")
+
+    @property
+    def step_count(self) -> int:
+        return int(self.lib.lb_step_count(self.ctx))
+
+    def moments(self, device: bool = False):
+        """(rho, (ux, uy, uz), T) as numpy [nz, ny, nx] arrays, or torch CUDA tensors if device."""
+        if device:
+            import torch
+            outs = [torch.empty(self.shape, dtype=torch.float64, device="cuda") for _ in range(5)]
+        else:
+            outs = [np.empty(self.shape, dtype=np.float64) for _ in range(5)]
+        self._check(self.lib.lb_moments(self.ctx, *[_ptr(o) for o in outs], int(device)), "lb_moments")
+        return outs[0], (outs[1], outs[2], outs[3]), outs[4]
+
+    def moments_into(self, rho=None, ux=None, uy=None, uz=None, T=None, device: bool = False):
+        self._check(self.lib.lb_moments(self.ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T),
+                                        int(device)), "lb_moments")
+
+    def nusselt(self):
+        """(Nu_mean, Nu(z) [nz], time average of the accumulated Nu_mean samples or NaN)."""
+        mean = ctypes.c_double()
+        avg = ctypes.c_double()
+        nu_z = np.empty(self.params.nz, dtype=np.float64)
+        self._check(self.lib.lb_nusselt(self.ctx, ctypes.byref(mean), _ptr(nu_z), ctypes.byref(avg)),
+                    "lb_nusselt")
+        return mean.value, nu_z, avg.value
+
+    def populations(self, device: bool = False):
+        """Pre-collision (f, g), each [19, nz, ny, nx] float64."""
+        shape = (Q,) + self.shape
+        if device:
+            import torch
+            f = torch.empty(shape, dtype=torch.float64, device="cuda")
+            g = torch.empty(shape, dtype=torch.float64, device="cuda")
+        else:
+            f = np.empty(shape, dtype=np.float64)
+            g = np.empty(shape, dtype=np.float64)
+        self._check(self.lib.lb_populations(self.ctx, _ptr(f), _ptr(g), int(device)), "lb_populations")
+        return f, g
+
+    def diagnostics(self) -> dict:
+        out = np.empty(5, dtype=np.float64)
+        self._check(self.lib.lb_diagnostics(self.ctx, _ptr(out)), "lb_diagnostics")
+        return {"min_rho": out[0], "min_T": out[1], "nonfinite": int(out[2]), "mass": out[3],
+                "energy": out[4]}
+
+    def save(self, path):
+        self._check(self.lib.lb_save(self.ctx, str(path).encode()), "lb_save")
+
+    def load(self, path):
+        self._check(self.lib.lb_load(self.ctx, str(path).encode()), "lb_load")
+
+    def close(self):
+        if self._ctx:
+            self.lib.lb_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
