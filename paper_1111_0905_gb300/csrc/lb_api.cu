@@ -1,0 +1,471 @@
+// lb_api.cu -- C ABI of the thermal pseudopotential D3Q19 lattice Boltzmann step (include/lb.h).
+//
+// Host side: parameter validation, device memory of the context (two ping-pong population
+// lattices per distribution, diagnostics scratch), launch geometry, checkpoints. Every step of
+// the method runs in the kernels of lb_kernels.cuh; this file only marshals and orders them.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_launch.cuh"
+
+namespace tlbm {
+
+// Diagnostics finalisation: per-plane sums over tiles in a fixed order, then Nu(z) of Eq. (4)
+// (normalised by kappa (T_d - T_u)/nz) and global min/sums. out layout:
+// [0, nz) Nu(z); nz: Nu_mean; nz+1: min rho; nz+2: min T; nz+3: non-finite count;
+// nz+4: sum rho; nz+5: sum rho T. If acc != null, acc[0] += Nu_mean, acc[1] += 1.
+__global__ void lb_diag_finalize(const double* __restrict__ part, int nz, int ntiles, int nxy,
+                                 double kappa, double T_d, double T_u, double* __restrict__ out,
+                                 double* __restrict__ acc) {
+  extern __shared__ double sh[];  // [nz] conv sums, [nz] T sums
+  double* sconv = sh;
+  double* sT = sh + nz;
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+    double c = 0.0, t = 0.0;
+    for (int k = 0; k < ntiles; ++k) {
+      c += part[((size_t)z * ntiles + k) * NPART + 0];
+      t += part[((size_t)z * ntiles + k) * NPART + 1];
+    }
+    sconv[z] = c; sT[z] = t;
+  }
+  __syncthreads();
+  const double norm = kappa * (T_d - T_u) / nz;
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+    const double Tp = (z + 1 < nz) ? sT[z + 1] : 2.0 * T_u * nxy - sT[nz - 1];
+    const double Tm = (z - 1 >= 0) ? sT[z - 1] : 2.0 * T_d * nxy - sT[0];
+    const double flux = (sconv[z] - kappa * 0.5 * (Tp - Tm)) / nxy;
+    out[z] = flux / norm;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0, mr = 1e300, mT = 1e300, bad = 0.0, sr = 0.0, sE = 0.0;
+    for (int z = 0; z < nz; ++z) s += out[z];
+    for (size_t k = 0; k < (size_t)nz * ntiles; ++k) {
+      const double* p = part + k * NPART;
+      sr += p[2]; sE += p[3]; mr = fmin(mr, p[4]); mT = fmin(mT, p[5]); bad += p[6];
+    }
+    const double mean = s / nz;
+    out[nz] = mean; out[nz + 1] = mr; out[nz + 2] = mT; out[nz + 3] = bad;
+    out[nz + 4] = sr; out[nz + 5] = sE;
+    if (acc) { acc[0] += mean; acc[1] += 1.0; }
+  }
+}
+
+
+// Validation of initial fields: per-block count of bad entries and sums (fixed order).
+__global__ void lb_validate_kernel(const double* __restrict__ rho, const double* __restrict__ T,
+                                   int N, double* __restrict__ out /* [gridDim.x][3] */) {
+  __shared__ double sh[3][256];
+  double bad = 0.0, sr = 0.0, sT = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double r = rho[i], t = T[i];
+    if (!(r > 0.0) || !(t > 0.0) || !isfinite(r) || !isfinite(t)) bad += 1.0;
+    sr += r; sT += t;
+  }
+  sh[0][threadIdx.x] = bad; sh[1][threadIdx.x] = sr; sh[2][threadIdx.x] = sT;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) out[blockIdx.x * 3 + k] = sh[k][0];
+}
+
+}  // namespace tlbm
+
+using namespace tlbm;
+
+struct lb_ctx {
+  lb_params p;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  const PrecOps* ops = nullptr;
+  void* f[2] = {nullptr, nullptr};
+  void* g[2] = {nullptr, nullptr};
+  int cur = 0;
+  int N = 0, plane = 0;
+  int by = 8, zc = 0, tiles_x = 0, tiles_y = 0, ntiles = 0, nchunks = 0;
+  double lam = 0.0, rho0 = 0.0, T0 = 0.0;
+  double* part = nullptr;    // [nz][ntiles][NPART]
+  double* diag = nullptr;    // [nz + 8]
+  double* nu_acc = nullptr;  // [2]
+  double* fields = nullptr;  // [5][N] staging for host-bound lb_moments
+  double* pops = nullptr;    // [38][N] staging for host-bound lb_populations
+  long long step = 0;
+  std::string err;
+};
+
+namespace {
+
+const char* kNullCtxMsg = "null context";
+
+int fail(lb_ctx* c, int code, const std::string& what) {
+  if (c) c->err = what;
+  return code;
+}
+int cuda_fail(lb_ctx* c, const char* where, cudaError_t e) {
+  return fail(c, LB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define LB_CU(ctx, call)                                        \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), #call, e_);  \
+  } while (0)
+
+const PrecOps* ops_for(int prec) {
+  switch (prec) {
+    case LB_FP64: return &kOpsF64;
+    case LB_FP32: return &kOpsF32;
+    case LB_BF16_DEV: return &kOpsBF16;
+    case LB_FP16_DEV: return &kOpsF16;
+    default: return nullptr;
+  }
+}
+
+KArgs make_args(const lb_ctx* c) {
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.fin = c->f[c->cur]; a.gin = c->g[c->cur];
+  a.fout = c->f[1 - c->cur]; a.gout = c->g[1 - c->cur];
+  a.nx = c->p.nx; a.ny = c->p.ny; a.nz = c->p.nz; a.plane = c->plane; a.N = c->N;
+  a.tiles_x = c->tiles_x; a.ntiles = c->ntiles; a.zc = c->zc;
+  a.tau_nu = c->p.tau_nu; a.omega_nu = 1.0 / c->p.tau_nu; a.omega_kappa = 1.0 / c->p.tau_kappa;
+  a.G = c->p.G; a.g_z = c->p.g_z; a.lam = c->lam; a.inv_cv = 1.0 / c->p.c_v; a.c_v = c->p.c_v;
+  a.kappa = c->p.kappa; a.T_d = c->p.T_d; a.T_u = c->p.T_u;
+  a.rho0 = c->rho0; a.E0 = c->rho0 * c->T0;
+  return a;
+}
+
+dim3 fused_grid(const lb_ctx* c) { return dim3(c->ntiles, c->nchunks); }
+
+void free_all(lb_ctx* c) {
+  if (!c) return;
+  for (int k = 0; k < 2; ++k) { cudaFree(c->f[k]); cudaFree(c->g[k]); }
+  cudaFree(c->part); cudaFree(c->diag); cudaFree(c->nu_acc);
+  cudaFree(c->fields); cudaFree(c->pops);
+}
+
+// Moments pass into the plane partials, then Nu(z) and the global health values into diag.
+int run_diag(lb_ctx* c, bool accumulate) {
+  KArgs a = make_args(c);
+  a.part = c->part;
+  LB_CU(c, c->ops->fused(a, MODE_MOMENTS, c->by, fused_grid(c), c->stream));
+  const int nz = c->p.nz;
+  lb_diag_finalize<<<1, 256, 2 * nz * sizeof(double), c->stream>>>(
+      c->part, nz, c->ntiles, c->p.nx * c->p.ny, c->p.kappa, c->p.T_d, c->p.T_u, c->diag,
+      accumulate ? c->nu_acc : nullptr);
+  LB_CU(c, cudaGetLastError());
+  return LB_OK;
+}
+
+uint64_t fnv1a(uint64_t h, const unsigned char* p, size_t n) {
+  for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+  return h;
+}
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, precision;
+  int32_t nx, ny, nz, pad;
+  int64_t step;
+  double rho0, T0;
+  double nu_acc[2];
+  lb_params params;
+  uint64_t checksum;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_strerror(int code) {
+  switch (code) {
+    case LB_OK: return "ok";
+    case LB_EINVAL: return "invalid argument";
+    case LB_ENOMEM: return "out of memory";
+    case LB_ECUDA: return "CUDA error";
+    case LB_ENONPHYS: return "non-physical state (rho <= 0, T <= 0 or NaN)";
+    case LB_EIO: return "checkpoint I/O error";
+    case LB_EUNSUP: return "unsupported";
+    default: return "unknown error";
+  }
+}
+
+const char* lb_last_error(const lb_ctx* c) { return c ? c->err.c_str() : kNullCtxMsg; }
+
+long long lb_step_count(const lb_ctx* c) { return c ? c->step : -1; }
+
+int lb_init(const lb_params* params, const double* rho_init, const double* T_init,
+            int init_on_device, void* cuda_stream, lb_ctx** out) {
+  if (!out) return LB_EINVAL;
+  *out = nullptr;
+  if (!params || !rho_init || !T_init) return LB_EINVAL;
+  const lb_params& p = *params;
+  if (p.nx < 1 || p.ny < 1 || p.nz < 1) return LB_EINVAL;
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  if (N >= (1ll << 31) || (long long)p.nz * 2 >= (1ll << 30)) return LB_EINVAL;
+  if (!(p.tau_nu > 0.5) || !(p.tau_kappa > 0.5) || !(p.kappa > 0.0) || !(p.c_v > 0.0)) return LB_EINVAL;
+  if (!std::isfinite(p.G) || !std::isfinite(p.g_z) || !(p.T_d > 0.0) || !(p.T_u > 0.0)) return LB_EINVAL;
+  const PrecOps* ops = ops_for(p.precision);
+  if (!ops) return LB_EINVAL;
+  int by = p.tile_y == 0 ? 8 : p.tile_y;
+  if (by != 4 && by != 8 && by != 16) return LB_EINVAL;
+  if (p.z_chunk < 0 || p.nu_every < 0 || p.check_every < 0) return LB_EINVAL;
+
+  lb_ctx* c = new (std::nothrow) lb_ctx();
+  if (!c) return LB_ENOMEM;
+  c->p = p;
+  c->ops = ops;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->N = (int)N;
+  c->plane = p.nx * p.ny;
+  c->by = by;
+  c->lam = p.kappa / (p.c_v * (p.tau_kappa - 0.5));
+  c->tiles_x = (p.nx + BX - 1) / BX;
+  c->tiles_y = (p.ny + by - 1) / by;
+  c->ntiles = c->tiles_x * c->tiles_y;
+  if (p.z_chunk > 0) {
+    c->zc = p.z_chunk < p.nz ? p.z_chunk : p.nz;
+  } else {
+    // enough CTAs to fill the 152 SMs about four times over, with at least 8 planes per chunk
+    const int target = 4 * 152;
+    int chunks = (target + c->ntiles - 1) / c->ntiles;
+    int maxchunks = (p.nz + 7) / 8;
+    if (chunks > maxchunks) chunks = maxchunks;
+    if (chunks < 1) chunks = 1;
+    c->zc = (p.nz + chunks - 1) / chunks;
+  }
+  c->nchunks = (p.nz + c->zc - 1) / c->zc;
+
+  auto bail = [&](int code) { free_all(c); delete c; return code; };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bail(LB_ECUDA);
+  if (ops->prepare() != cudaSuccess) return bail(LB_ECUDA);
+
+  // validate the initial fields and form their means on the device (fixed-order sums)
+  const double* d_rho = rho_init;
+  const double* d_T = T_init;
+  double* staging = nullptr;
+  const size_t fbytes = (size_t)N * sizeof(double);
+  if (!init_on_device) {
+    if (cudaMalloc(&staging, 2 * fbytes) != cudaSuccess) return bail(LB_ENOMEM);
+    if (cudaMemcpyAsync(staging, rho_init, fbytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(staging + N, T_init, fbytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+      cudaFree(staging);
+      return bail(LB_ECUDA);
+    }
+    d_rho = staging;
+    d_T = staging + N;
+  }
+  const int vblocks = 256;
+  double* vpart = nullptr;
+  if (cudaMalloc(&vpart, vblocks * 3 * sizeof(double)) != cudaSuccess) { cudaFree(staging); return bail(LB_ENOMEM); }
+  lb_validate_kernel<<<vblocks, 256, 0, c->stream>>>(d_rho, d_T, c->N, vpart);
+  std::vector<double> hv(vblocks * 3);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(hv.data(), vpart, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaFree(vpart); cudaFree(staging);
+    return bail(LB_ECUDA);
+  }
+  cudaFree(vpart);
+  double bad = 0, sr = 0, sT = 0;
+  for (int b = 0; b < vblocks; ++b) { bad += hv[b * 3]; sr += hv[b * 3 + 1]; sT += hv[b * 3 + 2]; }
+  if (bad > 0) { cudaFree(staging); return bail(LB_EINVAL); }
+  c->rho0 = p.rho0 > 0 ? p.rho0 : sr / N;
+  c->T0 = p.T0 > 0 ? p.T0 : sT / N;
+
+  const size_t pbytes = (size_t)Q * N * ops->esize;
+  for (int k = 0; k < 2; ++k) {
+    if (cudaMalloc(&c->f[k], pbytes) != cudaSuccess || cudaMalloc(&c->g[k], pbytes) != cudaSuccess) {
+      cudaFree(staging);
+      return bail(LB_ENOMEM);
+    }
+  }
+  if (cudaMalloc(&c->part, (size_t)p.nz * c->ntiles * NPART * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->diag, (size_t)(p.nz + 8) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->nu_acc, 2 * sizeof(double)) != cudaSuccess) {
+    cudaFree(staging);
+    return bail(LB_ENOMEM);
+  }
+  if (cudaMemsetAsync(c->nu_acc, 0, 2 * sizeof(double), c->stream) != cudaSuccess) { cudaFree(staging); return bail(LB_ECUDA); }
+  if (2 * p.nz * sizeof(double) > 48 * 1024 &&
+      cudaFuncSetAttribute(lb_diag_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(2 * p.nz * sizeof(double))) != cudaSuccess) {
+    cudaFree(staging);
+    return bail(LB_ECUDA);
+  }
+  c->cur = 0;
+  KArgs a = make_args(c);
+  a.fout = c->f[0]; a.gout = c->g[0];
+  if (ops->init(a, d_rho, d_T, c->stream) != cudaSuccess) { cudaFree(staging); return bail(LB_ECUDA); }
+  if (staging) {
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) { cudaFree(staging); return bail(LB_ECUDA); }
+    cudaFree(staging);
+  }
+  c->step = 0;
+  *out = c;
+  return LB_OK;
+}
+
+int lb_step(lb_ctx* c, long long nsteps) {
+  if (!c) return LB_EINVAL;
+  if (nsteps < 0) return fail(c, LB_EINVAL, "nsteps < 0");
+  const dim3 grid = fused_grid(c);
+  for (long long s = 0; s < nsteps; ++s) {
+    KArgs a = make_args(c);
+    LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, c->stream));
+    c->cur ^= 1;
+    c->step += 1;
+    if (c->p.nu_every > 0 && c->step % c->p.nu_every == 0) {
+      int rc = run_diag(c, true);
+      if (rc) return rc;
+    }
+    if (c->p.check_every > 0 && c->step % c->p.check_every == 0) {
+      int rc = run_diag(c, false);
+      if (rc) return rc;
+      double h[4];
+      LB_CU(c, cudaMemcpyAsync(h, c->diag + c->p.nz, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      LB_CU(c, cudaStreamSynchronize(c->stream));
+      if (!(h[1] > 0.0) || !(h[2] > 0.0) || h[3] != 0.0)
+        return fail(c, LB_ENONPHYS, "health check failed at step " + std::to_string(c->step));
+    }
+  }
+  return LB_OK;
+}
+
+int lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* uz, double* T, int on_device) {
+  if (!c) return LB_EINVAL;
+  KArgs a = make_args(c);
+  double* outs[5] = {rho, ux, uy, uz, T};
+  const size_t N = (size_t)c->N;
+  if (!on_device) {
+    if (!c->fields && cudaMalloc(&c->fields, 5 * N * sizeof(double)) != cudaSuccess)
+      return fail(c, LB_ENOMEM, "moments staging");
+    for (int k = 0; k < 5; ++k) if (outs[k]) outs[k] = c->fields + k * N;
+  }
+  a.rho_out = outs[0]; a.ux_out = outs[1]; a.uy_out = outs[2]; a.uz_out = outs[3]; a.T_out = outs[4];
+  a.part = nullptr;
+  LB_CU(c, c->ops->fused(a, MODE_MOMENTS, c->by, fused_grid(c), c->stream));
+  if (!on_device) {
+    double* host[5] = {rho, ux, uy, uz, T};
+    for (int k = 0; k < 5; ++k)
+      if (host[k])
+        LB_CU(c, cudaMemcpyAsync(host[k], c->fields + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CU(c, cudaStreamSynchronize(c->stream));
+  }
+  return LB_OK;
+}
+
+int lb_nusselt(lb_ctx* c, double* nu_mean, double* nu_z, double* nu_time_avg) {
+  if (!c || !nu_mean) return c ? fail(c, LB_EINVAL, "nu_mean is null") : LB_EINVAL;
+  int rc = run_diag(c, false);
+  if (rc) return rc;
+  const int nz = c->p.nz;
+  std::vector<double> h(nz + 1);
+  double acc[2];
+  LB_CU(c, cudaMemcpyAsync(h.data(), c->diag, (nz + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CU(c, cudaMemcpyAsync(acc, c->nu_acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CU(c, cudaStreamSynchronize(c->stream));
+  *nu_mean = h[nz];
+  if (nu_z) std::memcpy(nu_z, h.data(), nz * sizeof(double));
+  if (nu_time_avg) *nu_time_avg = acc[1] > 0 ? acc[0] / acc[1] : NAN;
+  return LB_OK;
+}
+
+int lb_diagnostics(lb_ctx* c, double out[5]) {
+  if (!c || !out) return c ? fail(c, LB_EINVAL, "out is null") : LB_EINVAL;
+  int rc = run_diag(c, false);
+  if (rc) return rc;
+  double h[5];
+  LB_CU(c, cudaMemcpyAsync(h, c->diag + c->p.nz + 1, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CU(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 5; ++k) out[k] = h[k];
+  return LB_OK;
+}
+
+int lb_populations(lb_ctx* c, double* f, double* g, int on_device) {
+  if (!c) return LB_EINVAL;
+  const size_t n = (size_t)Q * c->N;
+  double* df = f;
+  double* dg = g;
+  if (!on_device) {
+    if (!c->pops && cudaMalloc(&c->pops, 2 * n * sizeof(double)) != cudaSuccess)
+      return fail(c, LB_ENOMEM, "population staging");
+    df = f ? c->pops : nullptr;
+    dg = g ? c->pops + n : nullptr;
+  }
+  KArgs a = make_args(c);
+  LB_CU(c, c->ops->pops(a, df, dg, c->stream));
+  if (!on_device) {
+    if (f) LB_CU(c, cudaMemcpyAsync(f, df, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (g) LB_CU(c, cudaMemcpyAsync(g, dg, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CU(c, cudaStreamSynchronize(c->stream));
+  }
+  return LB_OK;
+}
+
+int lb_save(lb_ctx* c, const char* path) {
+  if (!c || !path) return c ? fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
+  const size_t pbytes = (size_t)Q * c->N * c->ops->esize;
+  std::vector<unsigned char> buf(2 * pbytes);
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "TLBMCKP1", 8);
+  h.version = 1; h.precision = c->p.precision;
+  h.nx = c->p.nx; h.ny = c->p.ny; h.nz = c->p.nz;
+  h.step = c->step; h.rho0 = c->rho0; h.T0 = c->T0; h.params = c->p;
+  LB_CU(c, cudaMemcpyAsync(buf.data(), c->f[c->cur], pbytes, cudaMemcpyDeviceToHost, c->stream));
+  LB_CU(c, cudaMemcpyAsync(buf.data() + pbytes, c->g[c->cur], pbytes, cudaMemcpyDeviceToHost, c->stream));
+  LB_CU(c, cudaMemcpyAsync(h.nu_acc, c->nu_acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CU(c, cudaStreamSynchronize(c->stream));
+  h.checksum = fnv1a(1469598103934665603ull, buf.data(), buf.size());
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(c, LB_EIO, std::string("cannot open ") + path);
+  bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+  ok = (std::fclose(fp) == 0) && ok;
+  return ok ? LB_OK : fail(c, LB_EIO, std::string("write failed: ") + path);
+}
+
+int lb_load(lb_ctx* c, const char* path) {
+  if (!c || !path) return c ? fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(c, LB_EIO, std::string("cannot open ") + path);
+  CkptHeader h;
+  const size_t pbytes = (size_t)Q * c->N * c->ops->esize;
+  std::vector<unsigned char> buf(2 * pbytes);
+  bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+  std::fclose(fp);
+  if (!ok) return fail(c, LB_EIO, "short read");
+  if (std::memcmp(h.magic, "TLBMCKP1", 8) != 0 || h.version != 1) return fail(c, LB_EIO, "bad magic/version");
+  if (h.nx != c->p.nx || h.ny != c->p.ny || h.nz != c->p.nz || h.precision != c->p.precision)
+    return fail(c, LB_EIO, "grid or precision mismatch");
+  if (fnv1a(1469598103934665603ull, buf.data(), buf.size()) != h.checksum)
+    return fail(c, LB_EIO, "checksum mismatch");
+  LB_CU(c, cudaMemcpyAsync(c->f[c->cur], buf.data(), pbytes, cudaMemcpyHostToDevice, c->stream));
+  LB_CU(c, cudaMemcpyAsync(c->g[c->cur], buf.data() + pbytes, pbytes, cudaMemcpyHostToDevice, c->stream));
+  LB_CU(c, cudaMemcpyAsync(c->nu_acc, h.nu_acc, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  LB_CU(c, cudaStreamSynchronize(c->stream));
+  c->step = h.step;
+  c->rho0 = h.rho0;
+  c->T0 = h.T0;
+  return LB_OK;
+}
+
+void lb_free(lb_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,494 @@
+// lb_kernels.cuh -- sm_103a kernels of the thermal pseudopotential D3Q19 lattice Boltzmann step.
+//
+// Biferale, Perlekar, Sbragaglia, Toschi, arXiv:1111.0905, "Algorithm" paragraph:
+// Eqs. (6)-(7) (two BGK lattice equations), Eq. (8) (moments), Eq. (9) (pseudopotential force
+// with psi = exp(-1/rho)), the velocity shift u' = u + tau_nu F/rho, the temperature from g in
+// the f equilibrium, and the counter term that yields the P0 div(u) term of Eq. (3).
+//
+// Storage: structure of arrays, population l of node idx at base[l*N + idx], idx = x + nx*(y + ny*z).
+// Streaming: pull with two lattices (ping-pong). The buffer between steps holds the
+// post-collision populations f*(n); the state at time n+1 is their pull plus the wall rules.
+//
+// Fused step kernel: one CTA owns a 32 x BY column tile and a range of z planes and marches up
+// in z. Per leading plane p it (M) pulls f on the tile plus a radius-2 ring and stores psi, rho,
+// j in shared memory; (U) for plane p-1 forms the force F and the physical velocity
+// u = (j + F/2)/rho on the tile plus a radius-1 ring; (C) for plane p-2 it pulls f and g of the
+// tile, takes div(u) from the three u planes and collides. Shared memory holds rolling windows
+// of 3 psi planes, 2 rho/j planes, 3 u planes and 2 F planes, so the only HBM traffic is the
+// populations (the ring pulls hit L1/L2).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace tlbm {
+
+constexpr int Q = 19;
+constexpr int BX = 32;      // tile width in x: one warp per row
+constexpr int NPART = 8;    // diagnostics partials per (plane, tile)
+
+// D3Q19: 0 rest; 1..6 axis (+-x, +-y, +-z); 7..10 xy diagonals; 11..14 xz; 15..18 yz.
+__host__ __device__ constexpr int CX(int l) {
+  return (l == 1 || l == 7 || l == 9 || l == 11 || l == 13) ? 1
+       : (l == 2 || l == 8 || l == 10 || l == 12 || l == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int CY(int l) {
+  return (l == 3 || l == 7 || l == 10 || l == 15 || l == 17) ? 1
+       : (l == 4 || l == 8 || l == 9 || l == 16 || l == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int CZ(int l) {
+  return (l == 5 || l == 11 || l == 14 || l == 15 || l == 18) ? 1
+       : (l == 6 || l == 12 || l == 13 || l == 16 || l == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int OPP(int l) { return l == 0 ? 0 : ((l & 1) ? l + 1 : l - 1); }
+__host__ __device__ constexpr int CSQ(int l) { return l == 0 ? 0 : (l <= 6 ? 1 : 2); }
+template <class R> __host__ __device__ constexpr R WT(int l) {
+  return l == 0 ? R(1) / R(3) : (l <= 6 ? R(1) / R(18) : R(1) / R(36));
+}
+// Force weights of Eq. (9): W(1) = 1/6, W(2) = 1/12 (isotropic to 4th order with D3Q19 links).
+template <class R> __host__ __device__ constexpr R FW(int l) {
+  return CSQ(l) == 1 ? R(1) / R(6) : R(1) / R(12);
+}
+
+// ---------------------------------------------------------------------------------------
+// Storage precision. Deviation forms store f_l - w_l*ref (ref = rho0 for f, rho0*T0 for g).
+// ---------------------------------------------------------------------------------------
+template <class S> struct Store;
+template <> struct Store<double> {
+  using R = double;
+  static __device__ __forceinline__ double ld(const double* p, double) { return __ldg(p); }
+  static __device__ __forceinline__ void st(double* p, double v, double) { *p = v; }
+  static __device__ __forceinline__ double rt(double v, double) { return v; }
+};
+template <> struct Store<float> {
+  using R = float;
+  static __device__ __forceinline__ float ld(const float* p, float) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
+  static __device__ __forceinline__ float rt(float v, float) { return v; }
+};
+template <> struct Store<__nv_bfloat16> {
+  using R = float;
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p, float base) {
+    return __bfloat162float(__ldg(p)) + base;
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v, float base) {
+    *p = __float2bfloat16_rn(v - base);
+  }
+  static __device__ __forceinline__ float rt(float v, float base) {
+    return __bfloat162float(__float2bfloat16_rn(v - base)) + base;
+  }
+};
+template <> struct Store<__half> {
+  using R = float;
+  static __device__ __forceinline__ float ld(const __half* p, float base) {
+    return __half2float(__ldg(p)) + base;
+  }
+  static __device__ __forceinline__ void st(__half* p, float v, float base) {
+    *p = __float2half_rn(v - base);
+  }
+  static __device__ __forceinline__ float rt(float v, float base) {
+    return __half2float(__float2half_rn(v - base)) + base;
+  }
+};
+
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+
+struct KArgs {
+  const void* fin; const void* gin;   // post-collision lattices of the previous step
+  void* fout; void* gout;             // lattices written by this step
+  int nx, ny, nz, plane, N;
+  int tiles_x, ntiles, zc;
+  double tau_nu, omega_nu, omega_kappa, G, g_z, lam, inv_cv, c_v, kappa, T_d, T_u;
+  double rho0, E0;                    // deviation references (rho0, rho0*T0)
+  // moments mode outputs (any may be null)
+  double* rho_out; double* ux_out; double* uy_out; double* uz_out; double* T_out;
+  double* part;                       // [nz][ntiles][NPART] diagnostics partials (may be null)
+};
+
+__host__ __device__ __forceinline__ int wrapi(int a, int n) { int m = a % n; return m < 0 ? m + n : m; }
+// Plane index of the reflection of plane k across the halfway walls (applied repeatedly).
+__host__ __device__ __forceinline__ int mirror_z(int k, int nz) {
+  int m = wrapi(k, 2 * nz);
+  return m < nz ? m : 2 * nz - 1 - m;
+}
+
+// Pull the 19 populations of node (col[1], row[1], pz): v_l = buf_l(x - c_l). Across a wall the
+// bounce-back source buf_{opp(l)}(x) is returned (the g wall rule is applied by the caller).
+template <class S, class R>
+__device__ __forceinline__ void pull(R (&v)[Q], const S* __restrict__ buf, int N, int pz, int nz,
+                                     int plane, const int (&col)[3], const int (&row)[3], R ref) {
+  const int own = pz * plane + row[1] + col[1];
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const int zs = pz - CZ(l);
+    const R base = WT<R>(l) * ref;
+    if (zs < 0 || zs >= nz) {
+      v[l] = Store<S>::ld(buf + (size_t)OPP(l) * N + own, base);
+    } else {
+      v[l] = Store<S>::ld(buf + (size_t)l * N + (zs * plane + row[1 - CY(l)] + col[1 - CX(l)]), base);
+    }
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void density_momentum(const R (&f)[Q], R& rho, R& jx, R& jy, R& jz) {
+  rho = f[0];
+#pragma unroll
+  for (int l = 1; l < Q; ++l) rho = rho + f[l];
+  // ascending l over the nonzero components
+  jx = f[1] - f[2]; jx = jx + f[7]; jx = jx - f[8]; jx = jx + f[9]; jx = jx - f[10];
+  jx = jx + f[11]; jx = jx - f[12]; jx = jx + f[13]; jx = jx - f[14];
+  jy = f[3] - f[4]; jy = jy + f[7]; jy = jy - f[8]; jy = jy - f[9]; jy = jy + f[10];
+  jy = jy + f[15]; jy = jy - f[16]; jy = jy + f[17]; jy = jy - f[18];
+  jz = f[5] - f[6]; jz = jz + f[11]; jz = jz - f[12]; jz = jz - f[13]; jz = jz + f[14];
+  jz = jz + f[15]; jz = jz - f[16]; jz = jz - f[17]; jz = jz + f[18];
+}
+
+// Even part of the rest equilibrium of g at the wall temperature (thermal anti-bounce-back):
+// w_l [rho T_w + 4.5 (lam T_w - rho T_w / 3)(|c_l|^2 - 1)].
+template <class R>
+__device__ __forceinline__ R wall_even(int l, R rho, R Tw, R lam) {
+  return WT<R>(l) * (rho * Tw + R(4.5) * (lam * Tw - rho * Tw / R(3)) * R(CSQ(l) - 1));
+}
+
+// Apply the thermal wall rule to pulled g of a node at plane z: for populations arriving
+// through a wall, g_l = -g*_{opp(l)} + 2 wall_even(l, rho_prev, T_w), rho_prev = sum of the
+// node's own post-collision f (its density at the colliding step).
+template <class S, class R>
+__device__ __forceinline__ void g_wall_fix(R (&g)[Q], const S* __restrict__ fin, int N, int own,
+                                           int z, int nz, R rho0, R Td, R Tu, R lam) {
+  if (z != 0 && z != nz - 1) return;
+  R rp = Store<S>::ld(fin + own, WT<R>(0) * rho0);
+#pragma unroll
+  for (int m = 1; m < Q; ++m) rp = rp + Store<S>::ld(fin + (size_t)m * N + own, WT<R>(m) * rho0);
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    if (CZ(l) > 0 && z == 0) g[l] = -g[l] + R(2) * wall_even<R>(l, rp, Td, lam);
+    if (CZ(l) < 0 && z == nz - 1) g[l] = -g[l] + R(2) * wall_even<R>(l, rp, Tu, lam);
+  }
+}
+
+enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
+
+template <int BY> struct Geo {
+  static constexpr int NT = BX * BY;
+  static constexpr int RX = BX + 4, RY = BY + 4, RXY = RX * RY;   // radius-2 ring (psi)
+  static constexpr int HX = BX + 2, HY = BY + 2, HXY = HX * HY;   // radius-1 ring (rho, j, u)
+  static constexpr int TXY = BX * BY;
+  static constexpr int MAXM = (RXY + NT - 1) / NT;
+  static constexpr int NHALO = 2 * BX + 2 * BY;
+  template <class R> static constexpr size_t smem_bytes() {
+    return sizeof(R) * (size_t)(3 * RXY + 8 * HXY + 9 * HXY + 6 * TXY);
+  }
+};
+
+__device__ __forceinline__ int slot3(int p) { return (p + 6) % 3; }
+__device__ __forceinline__ int slot2(int p) { return (p + 6) & 1; }
+
+template <class R> __device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <class R> __device__ __forceinline__ R warp_min(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <class S, int BY, int MODE>
+__global__ void __launch_bounds__(BX * BY)
+lb_fused_kernel(const KArgs a) {
+  using R = typename Store<S>::R;
+  using GE = Geo<BY>;
+  constexpr int NT = GE::NT, RX = GE::RX, RXY = GE::RXY, HX = GE::HX, HXY = GE::HXY;
+  constexpr int TXY = GE::TXY, MAXM = GE::MAXM, NHALO = GE::NHALO;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* psi_s = reinterpret_cast<R*>(smem_raw);  // [3][RXY]
+  R* rj_s = psi_s + 3 * RXY;                  // [2][4][HXY]  rho, jx, jy, jz
+  R* u_s = rj_s + 8 * HXY;                    // [3][3][HXY]  physical velocity
+  R* F_s = u_s + 9 * HXY;                     // [2][3][TXY]  force on the tile
+
+  const S* __restrict__ fin = static_cast<const S*>(a.fin);
+  const S* __restrict__ gin = static_cast<const S*>(a.gin);
+  const int nx = a.nx, ny = a.ny, nz = a.nz, plane = a.plane, N = a.N;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+  const int tile = blockIdx.x;
+  const int x0 = (tile % a.tiles_x) * BX, y0 = (tile / a.tiles_x) * BY;
+  const int z0 = blockIdx.y * a.zc;
+  const int z1 = min(z0 + a.zc, nz);
+
+  const R rho0 = R(a.rho0), E0 = R(a.E0);
+  const R G = R(a.G), gz = R(a.g_z), lam = R(a.lam), Td = R(a.T_d), Tu = R(a.T_u);
+
+  // Ring nodes of the M stage owned by this thread: wrapped columns/rows of x-1, x, x+1.
+  int mcol[MAXM][3], mrow[MAXM][3];
+  bool mrj[MAXM];
+#pragma unroll
+  for (int i = 0; i < MAXM; ++i) {
+    const int k = tid + i * NT;
+    const int rx = k % RX, ry = k / RX;
+    const int gx = x0 + rx - 2, gy = y0 + ry - 2;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      mcol[i][j] = wrapi(gx - 1 + j, nx);
+      mrow[i][j] = wrapi(gy - 1 + j, ny) * nx;
+    }
+    mrj[i] = (rx >= 1 && rx <= BX + 2 && ry >= 1 && ry <= BY + 2);
+  }
+  int ccol[3], crow[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    ccol[j] = wrapi(x0 + tx - 1 + j, nx);
+    crow[j] = wrapi(y0 + ty - 1 + j, ny) * nx;
+  }
+  const bool cvalid = (x0 + tx < nx) && (y0 + ty < ny);
+
+  // U-stage halo node of this thread (radius-1 ring minus corners), if any.
+  int hx = 0, hy = 0;
+  const bool has_halo = tid < NHALO;
+  if (tid < BX) { hx = tid; hy = -1; }
+  else if (tid < 2 * BX) { hx = tid - BX; hy = BY; }
+  else if (tid < 2 * BX + BY) { hx = -1; hy = tid - 2 * BX; }
+  else { hx = BX; hy = tid - 2 * BX - BY; }
+
+  for (int p = z0 - 2; p <= z1 + 1; ++p) {
+    // ---------------- M: psi, rho, j of plane p on the radius-2 ring ----------------
+    {
+      const int pz = mirror_z(p, nz);
+      const int s3 = slot3(p), s2 = slot2(p);
+#pragma unroll
+      for (int i = 0; i < MAXM; ++i) {
+        const int k = tid + i * NT;
+        if (k < RXY) {
+          R f[Q];
+          pull<S, R>(f, fin, N, pz, nz, plane, mcol[i], mrow[i], rho0);
+          R rho, jx, jy, jz;
+          density_momentum<R>(f, rho, jx, jy, jz);
+          psi_s[s3 * RXY + k] = dexp(R(-1) / rho);
+          if (mrj[i]) {
+            const int rx = k % RX, ry = k / RX;
+            const int h = (ry - 1) * HX + (rx - 1);
+            R* rj = rj_s + s2 * 4 * HXY;
+            rj[h] = rho; rj[HXY + h] = jx; rj[2 * HXY + h] = jy; rj[3 * HXY + h] = jz;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- U: F and u = (j + F/2)/rho of plane q = p-1 ----------------
+    {
+      const int q = p - 1;
+      if (q >= z0 - 1 && q <= z1 && q >= 0 && q < nz) {
+        const R* pm = psi_s + slot3(q - 1) * RXY;
+        const R* p0 = psi_s + slot3(q) * RXY;
+        const R* pp = psi_s + slot3(q + 1) * RXY;
+        const R* rj = rj_s + slot2(q) * 4 * HXY;
+        R* us = u_s + slot3(q) * 3 * HXY;
+        R* Fs = F_s + slot2(q) * 3 * TXY;
+        auto unode = [&](int xr, int yr, bool on_tile) {
+          const int c = (yr + 2) * RX + (xr + 2);
+          R ax = R(0), ay = R(0), az = R(0);
+#pragma unroll
+          for (int l = 1; l < Q; ++l) {
+            const R* pl = CZ(l) == 0 ? p0 : (CZ(l) > 0 ? pp : pm);
+            const R nb = pl[c + CY(l) * RX + CX(l)];
+            if (CX(l) != 0) ax = ax + (FW<R>(l) * R(CX(l))) * nb;
+            if (CY(l) != 0) ay = ay + (FW<R>(l) * R(CY(l))) * nb;
+            if (CZ(l) != 0) az = az + (FW<R>(l) * R(CZ(l))) * nb;
+          }
+          const int h = (yr + 1) * HX + (xr + 1);
+          const R rho = rj[h];
+          const R mg = -G * p0[c];
+          const R Fx = mg * ax, Fy = mg * ay, Fz = mg * az + rho * gz;
+          us[h] = (rj[HXY + h] + R(0.5) * Fx) / rho;
+          us[HXY + h] = (rj[2 * HXY + h] + R(0.5) * Fy) / rho;
+          us[2 * HXY + h] = (rj[3 * HXY + h] + R(0.5) * Fz) / rho;
+          if (on_tile) {
+            const int t = yr * BX + xr;
+            Fs[t] = Fx; Fs[TXY + t] = Fy; Fs[2 * TXY + t] = Fz;
+          }
+        };
+        unode(tx, ty, true);
+        if (has_halo) unode(hx, hy, false);
+      }
+    }
+    __syncthreads();
+    // ---------------- C: collide plane z = p-2 ----------------
+    const int z = p - 2;
+    const bool cplane = (z >= z0 && z < z1);
+    // moments-mode partials of this thread's node (neutral values when it has none)
+    double d_conv = 0.0, d_T = 0.0, d_rho = 0.0, d_E = 0.0, d_mr = 1e300, d_mT = 1e300, d_bad = 0.0;
+    if (cplane && cvalid) {
+      const int own = z * plane + crow[1] + ccol[1];
+      R f[Q], g[Q];
+      pull<S, R>(f, fin, N, z, nz, plane, ccol, crow, rho0);
+      pull<S, R>(g, gin, N, z, nz, plane, ccol, crow, E0);
+      g_wall_fix<S, R>(g, fin, N, own, z, nz, rho0, Td, Tu, lam);
+      R rho, jx, jy, jz;
+      density_momentum<R>(f, rho, jx, jy, jz);
+      R E = g[0];
+#pragma unroll
+      for (int l = 1; l < Q; ++l) E = E + g[l];
+      const R T = E / rho;
+      const R* u0 = u_s + slot3(z) * 3 * HXY;
+      const int cc = (ty + 1) * HX + (tx + 1);
+      const R ux = u0[cc], uy = u0[HXY + cc], uz = u0[2 * HXY + cc];
+      if constexpr (MODE == MODE_STEP) {
+        const int t = ty * BX + tx;
+        const R* Fs = F_s + slot2(z) * 3 * TXY;
+        const R Fx = Fs[t], Fy = Fs[TXY + t], Fz = Fs[2 * TXY + t];
+        const R* um = u_s + slot3(z - 1) * 3 * HXY;
+        const R* up = u_s + slot3(z + 1) * 3 * HXY;
+        const R uzm = (z - 1 >= 0) ? um[2 * HXY + cc] : -uz;
+        const R uzp = (z + 1 < nz) ? up[2 * HXY + cc] : -uz;
+        R D = R(0.5) * (u0[cc + 1] - u0[cc - 1]);
+        D = D + R(0.5) * (u0[HXY + cc + HX] - u0[HXY + cc - HX]);
+        D = D + R(0.5) * (uzp - uzm);
+        // f collision with the shifted velocity u' = (j + tau F)/rho and T in f^eq
+        const R tau = R(a.tau_nu), om = R(a.omega_nu), omk = R(a.omega_kappa);
+        const R vx = (jx + tau * Fx) / rho, vy = (jy + tau * Fy) / rho, vz = (jz + tau * Fz) / rho;
+        const R vv = vx * vx + vy * vy + vz * vz;
+        const R th = R(4.5) * (T - R(1) / R(3));
+        S* __restrict__ fo = static_cast<S*>(a.fout);
+        S* __restrict__ go = static_cast<S*>(a.gout);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
+          const R feq = WT<R>(l) * rho *
+              (R(1) + R(3) * cv + R(4.5) * cv * cv - R(1.5) * vv + th * R(CSQ(l) - 1));
+          Store<S>::st(fo + (size_t)l * N + own, f[l] + (feq - f[l]) * om, WT<R>(l) * rho0);
+        }
+        // g collision with the physical velocity and the counter term S = -rho T div(u)/c_v
+        const R uu = ux * ux + uy * uy + uz * uz;
+        const R Erho = rho * T;
+        const R Ssrc = -Erho * D * R(a.inv_cv);
+        const R lt = R(4.5) * (lam * T - Erho / R(3));
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const R cu = R(CX(l)) * ux + R(CY(l)) * uy + R(CZ(l)) * uz;
+          const R geq = WT<R>(l) * (Erho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu)
+                                    + lt * R(CSQ(l) - 1));
+          Store<S>::st(go + (size_t)l * N + own, g[l] + (geq - g[l]) * omk + WT<R>(l) * Ssrc,
+                       WT<R>(l) * E0);
+        }
+      } else {
+        if (a.rho_out) a.rho_out[own] = double(rho);
+        if (a.ux_out) a.ux_out[own] = double(ux);
+        if (a.uy_out) a.uy_out[own] = double(uy);
+        if (a.uz_out) a.uz_out[own] = double(uz);
+        if (a.T_out) a.T_out[own] = double(T);
+        const double drho = double(rho), dT = double(T), duz = double(uz);
+        const double U = a.c_v * dT + 0.25 * a.G * exp(-2.0 / drho);
+        d_conv = drho * U * duz; d_T = dT; d_rho = drho; d_E = drho * dT; d_mr = drho; d_mT = dT;
+        d_bad = (isfinite(drho) && isfinite(dT) && isfinite(double(ux)) && isfinite(double(uy)) &&
+                 isfinite(duz)) ? 0.0 : 1.0;
+      }
+    }
+    if constexpr (MODE == MODE_MOMENTS) {
+      if (a.part != nullptr && cplane) {
+        // FP64 warp-shuffle reduction of the plane partials, then across the BY warps
+        __shared__ double red[7][BY];
+        d_conv = warp_sum(d_conv); d_T = warp_sum(d_T); d_rho = warp_sum(d_rho);
+        d_E = warp_sum(d_E); d_mr = warp_min(d_mr); d_mT = warp_min(d_mT); d_bad = warp_sum(d_bad);
+        if (tx == 0) {
+          red[0][ty] = d_conv; red[1][ty] = d_T; red[2][ty] = d_rho; red[3][ty] = d_E;
+          red[4][ty] = d_mr; red[5][ty] = d_mT; red[6][ty] = d_bad;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double acc[7];
+          for (int k = 0; k < 7; ++k) acc[k] = red[k][0];
+          for (int w = 1; w < BY; ++w) {
+            for (int k = 0; k < 4; ++k) acc[k] += red[k][w];
+            acc[4] = fmin(acc[4], red[4][w]); acc[5] = fmin(acc[5], red[5][w]);
+            acc[6] += red[6][w];
+          }
+          double* out = a.part + ((size_t)z * a.ntiles + tile) * NPART;
+          for (int k = 0; k < 7; ++k) out[k] = acc[k];
+          out[7] = 0.0;
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Initial state: buffer B0 whose pull gives f = f^eq(rho, 0, T), g = g^eq(rho, T, 0).
+// B0_l(y) = eq_l(y + c_l) where y + c_l is inside, else the wall slot pulled back by the
+// bounce-back of opp(l) at y: f-slot = f^eq_{opp(l)}(y); g-slot chosen so that the thermal
+// wall rule returns g^eq_{opp(l)}(y) with rho_prev = sum_m B0f_m(y) (as stored).
+// ---------------------------------------------------------------------------------------
+template <class S>
+__global__ void lb_init_kernel(const KArgs a, const double* __restrict__ rho_in,
+                               const double* __restrict__ T_in) {
+  using R = typename Store<S>::R;
+  S* __restrict__ fo = static_cast<S*>(a.fout);
+  S* __restrict__ go = static_cast<S*>(a.gout);
+  const int nx = a.nx, ny = a.ny, nz = a.nz, plane = a.plane, N = a.N;
+  const R rho0 = R(a.rho0), E0 = R(a.E0), lam = R(a.lam);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+    const int x = idx % nx, y = (idx / nx) % ny, z = idx / plane;
+    R fb[Q];
+    bool wall[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const int zn = z + CZ(l);
+      wall[l] = (zn < 0 || zn >= nz);
+      const int src = wall[l] ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
+      const int le = wall[l] ? OPP(l) : l;   // equilibrium direction stored in this slot
+      const R r = R(rho_in[src]), T = R(T_in[src]);
+      const R feq = WT<R>(le) * r * (R(1) + R(4.5) * (T - R(1) / R(3)) * R(CSQ(le) - 1));
+      Store<S>::st(fo + (size_t)l * N + idx, feq, WT<R>(l) * rho0);
+      fb[l] = Store<S>::rt(feq, WT<R>(l) * rho0);   // the value a later load returns
+    }
+    // rho_prev exactly as the step kernel forms it from the stored values
+    R rp = fb[0];
+#pragma unroll
+    for (int m = 1; m < Q; ++m) rp = rp + fb[m];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const int zn = z + CZ(l);
+      const int src = wall[l] ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
+      const int le = wall[l] ? OPP(l) : l;
+      const R r = R(rho_in[src]), T = R(T_in[src]);
+      const R E = r * T;
+      R geq = WT<R>(le) * (E + R(4.5) * (lam * T - E / R(3)) * R(CSQ(le) - 1));
+      if (wall[l]) {
+        // slot l at y is pulled by direction le = opp(l), arriving through the wall at y
+        const R Tw = (CZ(le) > 0) ? R(a.T_d) : R(a.T_u);
+        geq = R(2) * wall_even<R>(le, rp, Tw, lam) - geq;
+      }
+      Store<S>::st(go + (size_t)l * N + idx, geq, WT<R>(l) * E0);
+    }
+  }
+}
+
+// Pre-collision state (pull + wall rules) exported as float64 [19][N].
+template <class S>
+__global__ void lb_pops_kernel(const KArgs a, double* __restrict__ fo, double* __restrict__ go) {
+  using R = typename Store<S>::R;
+  const S* __restrict__ fin = static_cast<const S*>(a.fin);
+  const S* __restrict__ gin = static_cast<const S*>(a.gin);
+  const int nx = a.nx, ny = a.ny, nz = a.nz, plane = a.plane, N = a.N;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+    const int x = idx % nx, y = (idx / nx) % ny, z = idx / plane;
+    int col[3], row[3];
+    for (int j = 0; j < 3; ++j) { col[j] = wrapi(x - 1 + j, nx); row[j] = wrapi(y - 1 + j, ny) * nx; }
+    R f[Q], g[Q];
+    pull<S, R>(f, fin, N, z, nz, plane, col, row, R(a.rho0));
+    pull<S, R>(g, gin, N, z, nz, plane, col, row, R(a.E0));
+    g_wall_fix<S, R>(g, fin, N, idx, z, nz, R(a.rho0), R(a.T_d), R(a.T_u), R(a.lam));
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      if (fo) fo[(size_t)l * N + idx] = double(f[l]);
+      if (go) go[(size_t)l * N + idx] = double(g[l]);
+    }
+  }
+}
+
+}  // namespace tlbm

@@ -1,0 +1,67 @@
+// lb_launch.cuh -- per-precision launch table of the kernels in lb_kernels.cuh.
+// Each precision is compiled in its own translation unit (lb_prec_*.cu) that defines one table.
+#pragma once
+#include "lb_kernels.cuh"
+
+namespace tlbm {
+
+struct PrecOps {
+  size_t esize;        // bytes per stored population
+  int deviation;       // 1 if populations are stored as deviations from w_l * ref
+  cudaError_t (*prepare)();   // per-device kernel attributes (call with the device current)
+  cudaError_t (*fused)(const KArgs&, int mode, int by, dim3 grid, cudaStream_t);
+  cudaError_t (*init)(const KArgs&, const double*, const double*, cudaStream_t);
+  cudaError_t (*pops)(const KArgs&, double*, double*, cudaStream_t);
+};
+
+extern const PrecOps kOpsF64, kOpsF32, kOpsBF16, kOpsF16;
+
+template <class S> struct OpsImpl {
+  using R = typename Store<S>::R;
+
+  template <int BY, int MODE> static cudaError_t attr() {
+    return cudaFuncSetAttribute(lb_fused_kernel<S, BY, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Geo<BY>::template smem_bytes<R>());
+  }
+  static cudaError_t prepare() {
+    cudaError_t e;
+    if ((e = attr<4, MODE_STEP>()) != cudaSuccess) return e;
+    if ((e = attr<8, MODE_STEP>()) != cudaSuccess) return e;
+    if ((e = attr<16, MODE_STEP>()) != cudaSuccess) return e;
+    if ((e = attr<4, MODE_MOMENTS>()) != cudaSuccess) return e;
+    if ((e = attr<8, MODE_MOMENTS>()) != cudaSuccess) return e;
+    return attr<16, MODE_MOMENTS>();
+  }
+  template <int BY, int MODE> static cudaError_t go(const KArgs& a, dim3 grid, cudaStream_t st) {
+    lb_fused_kernel<S, BY, MODE>
+        <<<grid, dim3(BX, BY), Geo<BY>::template smem_bytes<R>(), st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t fused(const KArgs& a, int mode, int by, dim3 grid, cudaStream_t st) {
+    if (mode == MODE_STEP) {
+      if (by == 4) return go<4, MODE_STEP>(a, grid, st);
+      if (by == 8) return go<8, MODE_STEP>(a, grid, st);
+      if (by == 16) return go<16, MODE_STEP>(a, grid, st);
+    } else {
+      if (by == 4) return go<4, MODE_MOMENTS>(a, grid, st);
+      if (by == 8) return go<8, MODE_MOMENTS>(a, grid, st);
+      if (by == 16) return go<16, MODE_MOMENTS>(a, grid, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+  static int blocks_for(int N) {
+    long long b = ((long long)N + 255) / 256;
+    return (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+  }
+  static cudaError_t init(const KArgs& a, const double* rho, const double* T, cudaStream_t st) {
+    lb_init_kernel<S><<<blocks_for(a.N), 256, 0, st>>>(a, rho, T);
+    return cudaGetLastError();
+  }
+  static cudaError_t pops(const KArgs& a, double* f, double* g, cudaStream_t st) {
+    lb_pops_kernel<S><<<blocks_for(a.N), 256, 0, st>>>(a, f, g);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace tlbm

@@ -1,0 +1,7 @@
+// Launch table of the __half population storage (see lb_launch.cuh).
+#include "lb_launch.cuh"
+
+namespace tlbm {
+const PrecOps kOpsF16 = {sizeof(__half), 1, &OpsImpl<__half>::prepare, &OpsImpl<__half>::fused,
+                    &OpsImpl<__half>::init, &OpsImpl<__half>::pops};
+}  // namespace tlbm

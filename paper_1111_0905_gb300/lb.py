@@ -151,13 +151,14 @@ class Lattice:
         self.shape = (params.nz, params.ny, params.nx)
         self._ctx = ctypes.c_void_p()
         n = params.N
-        on_device = not isinstance(rho, np.ndarray)
-        if on_device:
+        on_device = (not isinstance(rho, np.ndarray)) and bool(rho.is_cuda)
+        if not isinstance(rho, np.ndarray):
             import torch
-            rho = rho.to(torch.float64).contiguous()
-            T = T.to(torch.float64).contiguous()
-            if rho.numel() != n or T.numel() != n:
-                raise ValueError("field size does not match the grid")
+            if rho.dtype != torch.float64 or T.dtype != torch.float64:
+                raise ValueError("fields must be float64")
+            rho, T = rho.contiguous(), T.contiguous()
+            if rho.numel() != n or T.numel() != n or bool(T.is_cuda) != on_device:
+                raise ValueError("field size or placement does not match")
             self._keep = (rho, T)
         else:
             rho, T = _host_f64(rho, n), _host_f64(T, n)
@@ -200,6 +201,7 @@ class Lattice:
         return outs[0], (outs[1], outs[2], outs[3]), outs[4]
 
     def moments_into(self, rho=None, ux=None, uy=None, uz=None, T=None, device: bool = False):
+        """lb_moments into caller-owned buffers (numpy/pinned host tensors, or CUDA tensors)."""
         self._check(self.lib.lb_moments(self.ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T),
                                         int(device)), "lb_moments")
 

@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances: FP64 1e-12 of each field's scale after N steps; FP32 1e-5; 16-bit deviation
+storage 2e-3 on rho and T. Grids span several 32 x BY tiles, ragged tails in x, y and z,
+several z chunks, the degenerate nz = 1, 2 and the three tile heights.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lbm
+from paper_1111_0905_gb300 import config, lb, synthetic
+from helpers import oracle_params, oracle_run, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_run(p, rho, T, steps):
+    lat = lb.Lattice(p, rho, T)
+    lat.step(steps)
+    rho_g, u_g, T_g = lat.moments()
+    f_g, g_g = lat.populations()
+    nu = lat.nusselt()
+    return lat, rho_g, u_g, T_g, f_g, g_g, nu
+
+
+def _compare(p, rho, T, steps, tol, nu_tol=None, pops=True):
+    lat, rho_g, u_g, T_g, f_g, g_g, nu = _gpu_run(p, rho, T, steps)
+    f, g, op, _ = oracle_run(p, rho, T, steps)
+    r_o, u_o, T_o = lbm.moments_out(f, g, op)
+    errs = {"rho": rel_err(rho_g, r_o), "T": rel_err(T_g, T_o)}
+    for a in range(3):
+        errs[f"u{a}"] = rel_err(u_g[a], u_o[a])
+    if pops:
+        errs["f"] = rel_err(f_g, f)
+        errs["g"] = rel_err(g_g, g)
+    nu_o, nuz_o = lbm.nusselt(f, g, op)
+    errs["nu_z"] = float(np.abs(nu[1] - nuz_o.numpy()).max() / max(1.0, np.abs(nuz_o.numpy()).max()))
+    lat.close()
+    bad = {k: v for k, v in errs.items() if v > (nu_tol if (k == "nu_z" and nu_tol) else tol)}
+    assert not bad, f"errors above tolerance: {bad} (all: {errs})"
+    return errs
+
+
+GRIDS = [
+    # (nx, ny, nz, tile_y, z_chunk)
+    (4, 4, 4, 8, 0),
+    (5, 6, 7, 4, 3),
+    (33, 9, 7, 8, 2),       # two x tiles with a 1-wide tail, ragged y, chunks of 2
+    (40, 17, 10, 16, 4),
+    (8, 8, 1, 4, 0),        # single layer between the two walls
+    (8, 5, 2, 8, 1),
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,by,zc", GRIDS)
+def test_fp64_boiling_parity_small_grids(lblib, cuda, nx, ny, nz, by, zc):
+    w = config.boiling_cell(nx, nz=nz, ny=ny)
+    p = w.params
+    p.tile_y, p.z_chunk = by, zc
+    rho, T = w.fields()
+    _compare(p, rho, T, 12, 1e-12, nu_tol=1e-9)
+
+
+def test_init_state_is_the_equilibrium(lblib, cuda):
+    w = config.boiling_cell(12, nz=9, ny=7)
+    rho, T = w.fields()
+    lat = lb.Lattice(w.params, rho, T)
+    r, u, TT = lat.moments()
+    f, g = lat.populations()
+    op = oracle_params(w.params)
+    f0, g0 = lbm.init_state(torch.from_numpy(rho), torch.from_numpy(T), op)
+    assert rel_err(r, rho) < 1e-15 and rel_err(TT, T) < 1e-14
+    assert rel_err(f, f0) < 1e-15 and rel_err(g, g0) < 1e-14
+    lat.close()
+
+
+def test_fp64_boiling_cell_32_200_steps(lblib, cuda):
+    """The 32^3 boiling cell (phase separation inside the spinodal), 200 steps, 1e-12."""
+    w = config.boiling_cell(32)
+    rho, T = w.fields()
+    errs = _compare(w.params, rho, T, 200, 1e-12, nu_tol=1e-9, pops=False)
+    print("32^3 x 200 FP64 errors:", errs)
+
+
+def test_fp64_single_phase_full_size_128(lblib, cuda):
+    """Full 128^3 single-phase workload in the benchmark's launch configuration, 2 steps."""
+    w = config.single_phase_cell(128)
+    rho, T = w.fields()
+    _compare(w.params, rho, T, 2, 1e-12, nu_tol=1e-9, pops=False)
+
+
+def test_fp32_parity(lblib, cuda):
+    w = config.single_phase_cell(32, precision=lb.LB_FP32)
+    rho, T = w.fields()
+    errs = _compare(w.params, rho, T, 50, 1e-5, nu_tol=1e-3, pops=True)
+    print("FP32 errors:", errs)
+
+
+def test_fp32_boiling_parity(lblib, cuda):
+    w = config.boiling_cell(24, precision=lb.LB_FP32)
+    rho, T = w.fields()
+    errs = _compare(w.params, rho, T, 30, 1e-5, nu_tol=1e-2, pops=True)
+    print("FP32 boiling errors:", errs)
+
+
+@pytest.mark.parametrize("prec", [lb.LB_BF16_DEV, lb.LB_FP16_DEV])
+def test_16bit_deviation_storage(lblib, cuda, prec):
+    """rho and T within 2e-3 of the FP64 oracle after 50 steps of the single-phase cell."""
+    w = config.single_phase_cell(32, precision=prec)
+    rho, T = w.fields()
+    lat = lb.Lattice(w.params, rho, T)
+    lat.step(50)
+    r, u, TT = lat.moments()
+    f, g, op, _ = oracle_run(w.params, rho, T, 50)
+    r_o, u_o, T_o = lbm.moments_out(f, g, op)
+    e_rho = float(np.abs(r - r_o.numpy()).max() / np.abs(r_o.numpy()).max())
+    e_T = float(np.abs(TT - T_o.numpy()).max() / np.abs(T_o.numpy()).max())
+    print("16-bit", prec, e_rho, e_T)
+    assert e_rho < 2e-3 and e_T < 2e-3
+    lat.close()
+
+
+def test_nu_time_average_matches_oracle(lblib, cuda):
+    w = config.boiling_cell(16)
+    p = w.params
+    p.nu_every = 2
+    rho, T = w.fields()
+    lat = lb.Lattice(p, rho, T)
+    lat.step(10)
+    nu_mean, nu_z, avg = lat.nusselt()
+    _, _, _, samples = oracle_run(p, rho, T, 10, nu_every=2)
+    assert len(samples) == 5
+    assert abs(avg - np.mean(samples)) < 1e-9 * max(1.0, abs(np.mean(samples)))
+    lat.close()
+
+
+def test_mass_conserved_and_diagnostics(lblib, cuda):
+    w = config.boiling_cell(24)
+    rho, T = w.fields()
+    lat = lb.Lattice(w.params, rho, T)
+    d0 = lat.diagnostics()
+    assert abs(d0["mass"] - rho.sum()) < 1e-12 * rho.sum()
+    assert abs(d0["min_rho"] - rho.min()) < 1e-15 and d0["nonfinite"] == 0
+    lat.step(100)
+    d1 = lat.diagnostics()
+    assert abs(d1["mass"] - d0["mass"]) < 1e-13 * d0["mass"]
+    lat.close()
+
+
+def test_checkpoint_roundtrip_is_bitwise(lblib, cuda, tmp_path):
+    w = config.boiling_cell(16)
+    rho, T = w.fields()
+    a = lb.Lattice(w.params, rho, T)
+    a.step(20)
+    a.save(tmp_path / "c.bin")
+    a.step(30)
+    fa, ga = a.populations()
+    b = lb.Lattice(w.params, rho, T)
+    b.load(tmp_path / "c.bin")
+    assert b.step_count == 20
+    b.step(30)
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    # a corrupted file is rejected
+    raw = bytearray((tmp_path / "c.bin").read_bytes())
+    raw[-5] ^= 0xFF
+    (tmp_path / "bad.bin").write_bytes(bytes(raw))
+    with pytest.raises(lb.LBError) as e:
+        b.load(tmp_path / "bad.bin")
+    assert e.value.code == -5
+    a.close(); b.close()
+
+
+def test_health_check_reports_nonphysical_state(lblib, cuda):
+    """tau_nu = 0.55 is linearly unstable for this scheme: the periodic health check returns
+    LB_ENONPHYS (a host-side error code; nothing faults on the device)."""
+    w = config.boiling_cell(8)
+    p = w.params
+    p.tau_nu, p.tau_kappa, p.kappa, p.check_every = 0.55, 0.6, 0.02, 25
+    rho, T = w.fields()
+    lat = lb.Lattice(p, rho, T)
+    with pytest.raises(lb.LBError) as e:
+        lat.step(3000)
+    assert e.value.code == -4
+    lat.close()
+
+
+def test_invalid_arguments(lblib, cuda):
+    w = config.boiling_cell(8)
+    rho, T = w.fields()
+    bad = rho.copy()
+    bad[0, 0, 0] = -1.0
+    with pytest.raises(lb.LBError):
+        lb.Lattice(w.params, bad, T)
+    lat = lb.Lattice(w.params, rho, T)
+    with pytest.raises(lb.LBError):
+        lat.step(-1)
+    lat.close()
+
+
+def test_device_pointers_and_stream(lblib, cuda):
+    """Initial fields and outputs passed as device pointers give the same result as host ones."""
+    w = config.boiling_cell(16)
+    rho, T = w.fields()
+    a = lb.Lattice(w.params, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+    b = lb.Lattice(w.params, rho, T)
+    a.step(5); b.step(5)
+    ra, ua, Ta = a.moments(device=True)
+    rb, ub, Tb = b.moments()
+    assert np.array_equal(ra.cpu().numpy(), rb) and np.array_equal(Ta.cpu().numpy(), Tb)
+    a.close(); b.close()

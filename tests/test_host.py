@@ -1,0 +1,99 @@
+"""Host-side checks that need no GPU: the seeded generator, the workload helper against the
+oracle's EOS, the C-ABI library's exports and the binding's struct layout."""
+import ctypes
+import math
+import subprocess
+import textwrap
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_1111_0905_gb300 import config, lb, synthetic
+from oracle import eos
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def test_splitmix64_reference_outputs():
+    """First outputs of SplitMix64 with seed 0 (the published reference sequence)."""
+    got = [int(x) for x in synthetic.splitmix64(5, seed=0)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F,
+                   0xF88BB8A8724C81EC, 0x1B39896A51A8749B]
+
+
+def test_uniform_noise_range_and_order():
+    u = synthetic.uniform_pm1(100000)
+    assert u.min() >= -1.0 and u.max() < 1.0 and abs(u.mean()) < 0.01
+    f = synthetic.noise_field(4, 3, 2)
+    assert f.shape == (2, 3, 4)
+    assert np.array_equal(f.reshape(-1), synthetic.uniform_pm1(24))
+    assert np.array_equal(synthetic.uniform_pm1(5, offset=3), synthetic.uniform_pm1(8)[3:])
+
+
+def test_workload_helper_matches_oracle_thermodynamics():
+    for rho in (0.57, 1.5, 1.789, 2.3):
+        b, cp = config.beta_cp(rho, config.T_M)
+        assert abs(b - eos.beta(rho, config.T_M, config.G_DEFAULT)) < 1e-12 * abs(b)
+        assert abs(cp - eos.c_p(rho, config.T_M, config.G_DEFAULT)) < 1e-12 * cp
+    _, Tc, _ = eos.critical_point(config.G_DEFAULT)
+    assert abs(Tc - config.T_C) < 1e-15 and abs(config.T_M - 1.0 / 3.0) < 1e-15
+    w = config.single_phase_cell(128)
+    p = w.params
+    nu = config.T_M * (p.tau_nu - 0.5)
+    Ra = eos.rayleigh(-p.g_z, 2.30, config.T_M, config.G_DEFAULT, 128, p.T_d - p.T_u, p.kappa, nu)
+    Ra_max = config.max_rayleigh(128, p.T_d - p.T_u, p.kappa, nu, 2.30, config.T_M)
+    assert abs(Ra / (0.5 * Ra_max) - 1) < 1e-9
+    chi = p.kappa / (2.30 * eos.c_p(2.30, config.T_M, config.G_DEFAULT))
+    assert abs(nu / chi - 9.0) < 1e-9
+
+
+def test_library_builds_and_exports_every_declared_symbol(lblib):
+    header = (ROOT / "include" / "lb.h").read_text()
+    declared = set()
+    for name in lb.EXPORTS:
+        assert f"{name}(" in header
+        declared.add(name)
+    import re
+    in_header = set(re.findall(r"^\s*(?:int|void|long long|const char\*)\s+(lb_\w+)\(", header, re.M))
+    assert in_header == declared
+    out = subprocess.run(["nm", "-D", "--defined-only", str(lb.library_path())], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert declared <= exported
+    for name in declared:
+        assert hasattr(lblib, name)
+    assert lblib.lb_strerror(-4).decode().startswith("non-physical")
+    assert lblib.lb_step_count(None) == -1
+
+
+def test_lb_params_layout_matches_the_c_header(tmp_path):
+    """Offsets and size of lb_params as the C compiler lays it out equal the ctypes mirror."""
+    fields = [f[0] for f in lb.LbParams._fields_]
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"lb.h\"\nint main(void){\n"
+    src += f'printf("%zu\\n", sizeof(lb_params));\n'
+    for f in fields:
+        src += f'printf("%zu\\n", offsetof(lb_params, {f}));\n'
+    src += "return 0;}\n"
+    c = tmp_path / "layout.c"
+    c.write_text(src)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", str(ROOT / "include"), str(c), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(lb.LbParams)
+    for f, off in zip(fields, vals[1:]):
+        assert getattr(lb.LbParams, f).offset == off, f
+
+
+def test_init_rejects_invalid_parameters_without_a_gpu(lblib):
+    """Parameter validation happens before any device call."""
+    w = config.boiling_cell(4)
+    rho, T = w.fields()
+    bad = dict(tau_nu=0.5)
+    p = w.params
+    for field, val in [("tau_nu", 0.5), ("tau_kappa", 0.4), ("kappa", 0.0), ("tile_y", 5), ("precision", 7)]:
+        q = lb.Params(**{**p.__dict__, field: val})
+        with pytest.raises(lb.LBError) as e:
+            lb.Lattice(q, rho, T, stream=None)
+        assert e.value.code == -1
