@@ -51,7 +51,7 @@ typedef enum {
 } lb_precision;
 
 typedef struct {
-  int nx, ny, nz;         /* grid; each >= 1, nx*ny*nz < 2^31 */
+  int nx, ny, nz;         /* grid; each >= 1, 19*nx*ny*nz < 2^32 */
   double tau_nu;          /* f relaxation time, Eq. (6); > 1/2 */
   double tau_kappa;       /* g relaxation time, Eq. (7); > 1/2 */
   double G;               /* pseudopotential coupling of Eq. (9); bulk P = rho T + (G/2) e^{-2/rho} */
@@ -63,7 +63,8 @@ typedef struct {
   int precision;          /* lb_precision */
   int nu_every;           /* > 0: accumulate Nu_mean every nu_every steps into the time average */
   int check_every;        /* > 0: lb_step checks rho > 0, T > 0, no NaN every check_every steps */
-  int tile_y;             /* launch shape: CTA tile is 32 x tile_y (4, 8 or 16; 0 = default 8) */
+  int tile_y;             /* launch shape: CTA tile is 32 x tile_y (4, 8 or 16; 16 not with FP64;
+                             0 = default: 16 for FP32, 8 otherwise) */
   int z_chunk;            /* launch shape: planes per CTA (0 = choose from the grid size) */
 } lb_params;
 

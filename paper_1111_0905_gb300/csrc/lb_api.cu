@@ -142,7 +142,13 @@ KArgs make_args(const lb_ctx* c) {
   a.tau_nu = c->p.tau_nu; a.omega_nu = 1.0 / c->p.tau_nu; a.omega_kappa = 1.0 / c->p.tau_kappa;
   a.G = c->p.G; a.g_z = c->p.g_z; a.lam = c->lam; a.inv_cv = 1.0 / c->p.c_v; a.c_v = c->p.c_v;
   a.kappa = c->p.kappa; a.T_d = c->p.T_d; a.T_u = c->p.T_u;
-  a.rho0 = c->rho0; a.E0 = c->rho0 * c->T0;
+  a.rho0 = c->rho0; a.T0 = c->T0; a.E0 = c->rho0 * c->T0;
+  // reference equilibria per class (rest, axis, diagonal): f^eq(rho0, 0, T0), g^eq(rho0, T0, 0)
+  const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+  for (int k = 0; k < 3; ++k) {
+    a.fbase[k] = w[k] * c->rho0 * (1.0 + 4.5 * (c->T0 - 1.0 / 3.0) * (k - 1));
+    a.gbase[k] = w[k] * (a.E0 + 4.5 * (c->lam * c->T0 - a.E0 / 3.0) * (k - 1));
+  }
   return a;
 }
 
@@ -218,8 +224,11 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   if (!std::isfinite(p.G) || !std::isfinite(p.g_z) || !(p.T_d > 0.0) || !(p.T_u > 0.0)) return LB_EINVAL;
   const PrecOps* ops = ops_for(p.precision);
   if (!ops) return LB_EINVAL;
-  int by = p.tile_y == 0 ? 8 : p.tile_y;
+  // default tile height: 32 x 16 for FP32, 32 x 8 otherwise (measured best on the 128^3/256^3 cells)
+  int by = p.tile_y != 0 ? p.tile_y : (p.precision == LB_FP32 ? 16 : 8);
   if (by != 4 && by != 8 && by != 16) return LB_EINVAL;
+  if (!ops->tile_ok(by)) return LB_EINVAL;
+  if ((long long)Q * N >= (1ll << 32)) return LB_EINVAL;   // 32-bit population offsets
   if (p.z_chunk < 0 || p.nu_every < 0 || p.check_every < 0) return LB_EINVAL;
 
   lb_ctx* c = new (std::nothrow) lb_ctx();
@@ -237,13 +246,9 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   if (p.z_chunk > 0) {
     c->zc = p.z_chunk < p.nz ? p.z_chunk : p.nz;
   } else {
-    // enough CTAs to fill the 152 SMs about four times over, with at least 8 planes per chunk
-    const int target = 4 * 152;
-    int chunks = (target + c->ntiles - 1) / c->ntiles;
-    int maxchunks = (p.nz + 7) / 8;
-    if (chunks > maxchunks) chunks = maxchunks;
-    if (chunks < 1) chunks = 1;
-    c->zc = (p.nz + chunks - 1) / chunks;
+    // 32 planes per chunk: the 4 prologue planes of a chunk cost 1/8 extra ring pulls, and the
+    // 128^3 and 256^3 cells keep every SM busy (measured best of 8..256)
+    c->zc = p.nz < 32 ? p.nz : 32;
   }
   c->nchunks = (p.nz + c->zc - 1) / c->zc;
 

@@ -52,48 +52,36 @@ template <class R> __host__ __device__ constexpr R FW(int l) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Storage precision. Deviation forms store f_l - w_l*ref (ref = rho0 for f, rho0*T0 for g).
+// Storage precision. Every form stores deviations from the reference equilibria,
+// df_l = f_l - f^eq_l(rho0, 0, T0) and dg_l = g_l - g^eq_l(rho0, T0, 0), so that the moments
+// and the collision work on small numbers (the 16-bit forms need it; FP32 gains accuracy).
 // ---------------------------------------------------------------------------------------
 template <class S> struct Store;
 template <> struct Store<double> {
   using R = double;
-  static __device__ __forceinline__ double ld(const double* p, double) { return __ldg(p); }
-  static __device__ __forceinline__ void st(double* p, double v, double) { *p = v; }
-  static __device__ __forceinline__ double rt(double v, double) { return v; }
+  static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+  static __device__ __forceinline__ double rt(double v) { return v; }
 };
 template <> struct Store<float> {
   using R = float;
-  static __device__ __forceinline__ float ld(const float* p, float) { return __ldg(p); }
-  static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
-  static __device__ __forceinline__ float rt(float v, float) { return v; }
+  static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+  static __device__ __forceinline__ float rt(float v) { return v; }
 };
 template <> struct Store<__nv_bfloat16> {
   using R = float;
-  static __device__ __forceinline__ float ld(const __nv_bfloat16* p, float base) {
-    return __bfloat162float(__ldg(p)) + base;
-  }
-  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v, float base) {
-    *p = __float2bfloat16_rn(v - base);
-  }
-  static __device__ __forceinline__ float rt(float v, float base) {
-    return __bfloat162float(__float2bfloat16_rn(v - base)) + base;
-  }
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float rt(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 template <> struct Store<__half> {
   using R = float;
-  static __device__ __forceinline__ float ld(const __half* p, float base) {
-    return __half2float(__ldg(p)) + base;
-  }
-  static __device__ __forceinline__ void st(__half* p, float v, float base) {
-    *p = __float2half_rn(v - base);
-  }
-  static __device__ __forceinline__ float rt(float v, float base) {
-    return __half2float(__float2half_rn(v - base)) + base;
-  }
+  static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+  static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
 };
 
-__device__ __forceinline__ double dexp(double x) { return exp(x); }
-__device__ __forceinline__ float dexp(float x) { return expf(x); }
 
 struct KArgs {
   const void* fin; const void* gin;   // post-collision lattices of the previous step
@@ -101,7 +89,8 @@ struct KArgs {
   int nx, ny, nz, plane, N;
   int tiles_x, ntiles, zc;
   double tau_nu, omega_nu, omega_kappa, G, g_z, lam, inv_cv, c_v, kappa, T_d, T_u;
-  double rho0, E0;                    // deviation references (rho0, rho0*T0)
+  double rho0, T0, E0;                // reference state of the deviations (E0 = rho0 T0)
+  double fbase[3], gbase[3];          // f^eq(rho0,0,T0), g^eq(rho0,T0,0) per class: rest, axis, diagonal
   // moments mode outputs (any may be null)
   double* rho_out; double* ux_out; double* uy_out; double* uz_out; double* T_out;
   double* part;                       // [nz][ntiles][NPART] diagnostics partials (may be null)
@@ -118,20 +107,24 @@ __host__ __device__ __forceinline__ int mirror_z(int k, int nz) {
 // bounce-back source buf_{opp(l)}(x) is returned (the g wall rule is applied by the caller).
 template <class S, class R>
 __device__ __forceinline__ void pull(R (&v)[Q], const S* __restrict__ buf, int N, int pz, int nz,
-                                     int plane, const int (&col)[3], const int (&row)[3], R ref) {
+                                     int plane, const int (&col)[3], const int (&row)[3]) {
   const int own = pz * plane + row[1] + col[1];
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
     const int zs = pz - CZ(l);
-    const R base = WT<R>(l) * ref;
     if (zs < 0 || zs >= nz) {
-      v[l] = Store<S>::ld(buf + (size_t)OPP(l) * N + own, base);
+      v[l] = Store<S>::ld(buf + (size_t)OPP(l) * N + own);
     } else {
-      v[l] = Store<S>::ld(buf + (size_t)l * N + (zs * plane + row[1 - CY(l)] + col[1 - CX(l)]), base);
+      v[l] = Store<S>::ld(buf + (size_t)l * N + (zs * plane + row[1 - CY(l)] + col[1 - CX(l)]));
     }
   }
 }
 
+// class of direction l: 0 rest, 1 axis, 2 diagonal (= |c_l|^2)
+__host__ __device__ constexpr int CLS(int l) { return CSQ(l); }
+
+// Sums of the deviations: drho = sum_l df_l (rho = rho0 + drho), j = sum_l c_l df_l (the reference
+// equilibrium carries no momentum), ascending l.
 template <class R>
 __device__ __forceinline__ void density_momentum(const R (&f)[Q], R& rho, R& jx, R& jy, R& jz) {
   rho = f[0];
@@ -146,31 +139,38 @@ __device__ __forceinline__ void density_momentum(const R (&f)[Q], R& rho, R& jx,
   jz = jz + f[15]; jz = jz - f[16]; jz = jz - f[17]; jz = jz + f[18];
 }
 
-// Even part of the rest equilibrium of g at the wall temperature (thermal anti-bounce-back):
-// w_l [rho T_w + 4.5 (lam T_w - rho T_w / 3)(|c_l|^2 - 1)].
+// Thermal wall rule (anti-bounce-back with the even part of g^eq at the wall temperature T_w):
+// g_l = -g*_{opp(l)} + 2 w_l [rho_p T_w + 4.5 (lam T_w - rho_p T_w / 3)(|c_l|^2 - 1)], rho_p = the wall
+// node's density at the colliding step = sum of its own post-collision f. In deviations:
+// dg_l = -dg*_{opp(l)} + 2 (wall_even_l - gbase_l).
 template <class R>
-__device__ __forceinline__ R wall_even(int l, R rho, R Tw, R lam) {
-  return WT<R>(l) * (rho * Tw + R(4.5) * (lam * Tw - rho * Tw / R(3)) * R(CSQ(l) - 1));
+__device__ __forceinline__ R wall_even_dev(int l, R drho_p, R rho0, R T0, R Tw, R lam) {
+  const R dP = drho_p * Tw + rho0 * (Tw - T0);   // rho_p T_w - rho0 T0
+  return WT<R>(l) * (dP + R(4.5) * (lam * (Tw - T0) - dP / R(3)) * R(CSQ(l) - 1));
 }
 
-// Apply the thermal wall rule to pulled g of a node at plane z: for populations arriving
-// through a wall, g_l = -g*_{opp(l)} + 2 wall_even(l, rho_prev, T_w), rho_prev = sum of the
-// node's own post-collision f (its density at the colliding step).
 template <class S, class R>
 __device__ __forceinline__ void g_wall_fix(R (&g)[Q], const S* __restrict__ fin, int N, int own,
-                                           int z, int nz, R rho0, R Td, R Tu, R lam) {
+                                           int z, int nz, R rho0, R T0, R Td, R Tu, R lam) {
   if (z != 0 && z != nz - 1) return;
-  R rp = Store<S>::ld(fin + own, WT<R>(0) * rho0);
+  R dp = Store<S>::ld(fin + own);
 #pragma unroll
-  for (int m = 1; m < Q; ++m) rp = rp + Store<S>::ld(fin + (size_t)m * N + own, WT<R>(m) * rho0);
+  for (int m = 1; m < Q; ++m) dp = dp + Store<S>::ld(fin + (size_t)m * N + own);
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
-    if (CZ(l) > 0 && z == 0) g[l] = -g[l] + R(2) * wall_even<R>(l, rp, Td, lam);
-    if (CZ(l) < 0 && z == nz - 1) g[l] = -g[l] + R(2) * wall_even<R>(l, rp, Tu, lam);
+    if (CZ(l) > 0 && z == 0) g[l] = -g[l] + R(2) * wall_even_dev<R>(l, dp, rho0, T0, Td, lam);
+    if (CZ(l) < 0 && z == nz - 1) g[l] = -g[l] + R(2) * wall_even_dev<R>(l, dp, rho0, T0, Tu, lam);
   }
 }
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
+
+// Reciprocal and exponential per compute precision: IEEE for FP64 (parity form); the rounded
+// MUFU-based forms for FP32 (relative error ~1e-7, far below the FP32 form's tolerance).
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
 
 template <int BY> struct Geo {
   static constexpr int NT = BX * BY;
@@ -179,8 +179,13 @@ template <int BY> struct Geo {
   static constexpr int TXY = BX * BY;
   static constexpr int MAXM = (RXY + NT - 1) / NT;
   static constexpr int NHALO = 2 * BX + 2 * BY;
-  template <class R> static constexpr size_t smem_bytes() {
-    return sizeof(R) * (size_t)(3 * RXY + 8 * HXY + 9 * HXY + 6 * TXY);
+  // R units: psi[3][RXY], rj[3][5][HXY] (rho, 1/rho, jx, jy, jz), u[3][3][HXY], F[2][3][TXY];
+  // then the pulled-f cache of the tile, fc[3][Q][TXY] in storage units S.
+  template <class R> static constexpr size_t r_count() {
+    return (size_t)(3 * RXY + 15 * HXY + 9 * HXY + 6 * TXY);
+  }
+  template <class S, class R> static constexpr size_t smem_bytes() {
+    return sizeof(R) * r_count<R>() + sizeof(S) * (size_t)(3 * Q * TXY);
   }
 };
 
@@ -198,8 +203,38 @@ template <class R> __device__ __forceinline__ R warp_min(R v) {
   return v;
 }
 
+// Pull the raw stored deviations of node (col[1], row[1], pz): v_l = buf_l(x - c_l); across a wall
+// (only when WALL) the bounce-back source buf_{opp(l)}(x). Element offsets are 32-bit (19 N < 2^32).
+template <class S, bool WALL>
+__device__ __forceinline__ void pull_raw(S (&v)[Q], const S* __restrict__ buf, unsigned N, int pz,
+                                         int nz, unsigned plane, const int (&col)[3], const int (&row)[3]) {
+  const unsigned zb = (unsigned)pz * plane;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const int cz = CZ(l);
+    if (WALL && ((cz > 0 && pz == 0) || (cz < 0 && pz == nz - 1))) {
+      v[l] = buf[(unsigned)OPP(l) * N + zb + (unsigned)(row[1] + col[1])];
+    } else {
+      v[l] = buf[(unsigned)l * N + (zb - (unsigned)(cz * (int)plane)) +
+                 (unsigned)(row[1 - CY(l)] + col[1 - CX(l)])];
+    }
+  }
+}
+
+template <class S, class R>
+__device__ __forceinline__ R cvt(S v) { return Store<S>::ld(&v); }
+template <> __device__ __forceinline__ double cvt<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float cvt<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ float cvt<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float cvt<__half, float>(__half v) { return __half2float(v); }
+
+// Resident CTAs per SM the register allocation must allow: 512 threads per SM for the FP32 and
+// 16-bit forms (128 registers a thread); the FP64 form is limited by its shared memory anyway.
+template <class S, int BY> struct MinBlocks { static constexpr int v = 512 / (BX * BY) > 0 ? 512 / (BX * BY) : 1; };
+template <int BY> struct MinBlocks<double, BY> { static constexpr int v = 1; };
+
 template <class S, int BY, int MODE>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, MinBlocks<S, BY>::v)
 lb_fused_kernel(const KArgs a) {
   using R = typename Store<S>::R;
   using GE = Geo<BY>;
@@ -208,25 +243,27 @@ lb_fused_kernel(const KArgs a) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* psi_s = reinterpret_cast<R*>(smem_raw);  // [3][RXY]
-  R* rj_s = psi_s + 3 * RXY;                  // [2][4][HXY]  rho, jx, jy, jz
-  R* u_s = rj_s + 8 * HXY;                    // [3][3][HXY]  physical velocity
+  R* rj_s = psi_s + 3 * RXY;                  // [3][5][HXY]  rho, 1/rho, jx, jy, jz
+  R* u_s = rj_s + 15 * HXY;                   // [3][3][HXY]  physical velocity
   R* F_s = u_s + 9 * HXY;                     // [2][3][TXY]  force on the tile
+  S* fc_s = reinterpret_cast<S*>(F_s + 6 * TXY);  // [3][Q][TXY] pulled f of the tile
 
   const S* __restrict__ fin = static_cast<const S*>(a.fin);
   const S* __restrict__ gin = static_cast<const S*>(a.gin);
-  const int nx = a.nx, ny = a.ny, nz = a.nz, plane = a.plane, N = a.N;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const unsigned plane = (unsigned)a.plane, N = (unsigned)a.N;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
   const int tile = blockIdx.x;
   const int x0 = (tile % a.tiles_x) * BX, y0 = (tile / a.tiles_x) * BY;
   const int z0 = blockIdx.y * a.zc;
   const int z1 = min(z0 + a.zc, nz);
 
-  const R rho0 = R(a.rho0), E0 = R(a.E0);
+  const R rho0 = R(a.rho0), E0 = R(a.E0), T0 = R(a.T0);
   const R G = R(a.G), gz = R(a.g_z), lam = R(a.lam), Td = R(a.T_d), Tu = R(a.T_u);
 
   // Ring nodes of the M stage owned by this thread: wrapped columns/rows of x-1, x, x+1.
   int mcol[MAXM][3], mrow[MAXM][3];
-  bool mrj[MAXM];
+  short mh[MAXM], mt[MAXM];   // index in the radius-1 ring / in the tile, or -1
 #pragma unroll
   for (int i = 0; i < MAXM; ++i) {
     const int k = tid + i * NT;
@@ -237,7 +274,8 @@ lb_fused_kernel(const KArgs a) {
       mcol[i][j] = wrapi(gx - 1 + j, nx);
       mrow[i][j] = wrapi(gy - 1 + j, ny) * nx;
     }
-    mrj[i] = (rx >= 1 && rx <= BX + 2 && ry >= 1 && ry <= BY + 2);
+    mh[i] = (k < RXY && rx >= 1 && rx <= BX + 2 && ry >= 1 && ry <= BY + 2) ? (short)((ry - 1) * HX + (rx - 1)) : (short)-1;
+    mt[i] = (k < RXY && rx >= 2 && rx < BX + 2 && ry >= 2 && ry < BY + 2) ? (short)((ry - 2) * BX + (rx - 2)) : (short)-1;
   }
   int ccol[3], crow[3];
 #pragma unroll
@@ -256,24 +294,35 @@ lb_fused_kernel(const KArgs a) {
   else { hx = BX; hy = tid - 2 * BX - BY; }
 
   for (int p = z0 - 2; p <= z1 + 1; ++p) {
-    // ---------------- M: psi, rho, j of plane p on the radius-2 ring ----------------
+    // ---------------- M: psi, rho, j of plane p on the radius-2 ring; f of the tile cached ----------------
     {
       const int pz = mirror_z(p, nz);
-      const int s3 = slot3(p), s2 = slot2(p);
+      const bool wallp = (pz == 0 || pz == nz - 1);
+      const bool real = (p == pz);
+      const int s3 = slot3(p);
 #pragma unroll
       for (int i = 0; i < MAXM; ++i) {
         const int k = tid + i * NT;
         if (k < RXY) {
+          S fr[Q];
+          if (wallp) pull_raw<S, true>(fr, fin, N, pz, nz, plane, mcol[i], mrow[i]);
+          else pull_raw<S, false>(fr, fin, N, pz, nz, plane, mcol[i], mrow[i]);
           R f[Q];
-          pull<S, R>(f, fin, N, pz, nz, plane, mcol[i], mrow[i], rho0);
-          R rho, jx, jy, jz;
-          density_momentum<R>(f, rho, jx, jy, jz);
-          psi_s[s3 * RXY + k] = dexp(R(-1) / rho);
-          if (mrj[i]) {
-            const int rx = k % RX, ry = k / RX;
-            const int h = (ry - 1) * HX + (rx - 1);
-            R* rj = rj_s + s2 * 4 * HXY;
-            rj[h] = rho; rj[HXY + h] = jx; rj[2 * HXY + h] = jy; rj[3 * HXY + h] = jz;
+#pragma unroll
+          for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fr[l]);
+          R drho, jx, jy, jz;
+          density_momentum<R>(f, drho, jx, jy, jz);
+          const R rho = rho0 + drho;
+          const R inv = rcp(rho);
+          psi_s[s3 * RXY + k] = fexp(-inv);
+          if (mh[i] >= 0) {
+            R* rj = rj_s + s3 * 5 * HXY + mh[i];
+            rj[0] = rho; rj[HXY] = inv; rj[2 * HXY] = jx; rj[3 * HXY] = jy; rj[4 * HXY] = jz;
+          }
+          if (real && mt[i] >= 0) {
+            S* fc = fc_s + s3 * Q * TXY + mt[i];
+#pragma unroll
+            for (int l = 0; l < Q; ++l) fc[l * TXY] = fr[l];
           }
         }
       }
@@ -286,7 +335,7 @@ lb_fused_kernel(const KArgs a) {
         const R* pm = psi_s + slot3(q - 1) * RXY;
         const R* p0 = psi_s + slot3(q) * RXY;
         const R* pp = psi_s + slot3(q + 1) * RXY;
-        const R* rj = rj_s + slot2(q) * 4 * HXY;
+        const R* rj = rj_s + slot3(q) * 5 * HXY;
         R* us = u_s + slot3(q) * 3 * HXY;
         R* Fs = F_s + slot2(q) * 3 * TXY;
         auto unode = [&](int xr, int yr, bool on_tile) {
@@ -301,12 +350,12 @@ lb_fused_kernel(const KArgs a) {
             if (CZ(l) != 0) az = az + (FW<R>(l) * R(CZ(l))) * nb;
           }
           const int h = (yr + 1) * HX + (xr + 1);
-          const R rho = rj[h];
+          const R rho = rj[h], inv = rj[HXY + h];
           const R mg = -G * p0[c];
           const R Fx = mg * ax, Fy = mg * ay, Fz = mg * az + rho * gz;
-          us[h] = (rj[HXY + h] + R(0.5) * Fx) / rho;
-          us[HXY + h] = (rj[2 * HXY + h] + R(0.5) * Fy) / rho;
-          us[2 * HXY + h] = (rj[3 * HXY + h] + R(0.5) * Fz) / rho;
+          us[h] = (rj[2 * HXY + h] + R(0.5) * Fx) * inv;
+          us[HXY + h] = (rj[3 * HXY + h] + R(0.5) * Fy) * inv;
+          us[2 * HXY + h] = (rj[4 * HXY + h] + R(0.5) * Fz) * inv;
           if (on_tile) {
             const int t = yr * BX + xr;
             Fs[t] = Fx; Fs[TXY + t] = Fy; Fs[2 * TXY + t] = Fz;
@@ -323,22 +372,33 @@ lb_fused_kernel(const KArgs a) {
     // moments-mode partials of this thread's node (neutral values when it has none)
     double d_conv = 0.0, d_T = 0.0, d_rho = 0.0, d_E = 0.0, d_mr = 1e300, d_mT = 1e300, d_bad = 0.0;
     if (cplane && cvalid) {
-      const int own = z * plane + crow[1] + ccol[1];
-      R f[Q], g[Q];
-      pull<S, R>(f, fin, N, z, nz, plane, ccol, crow, rho0);
-      pull<S, R>(g, gin, N, z, nz, plane, ccol, crow, E0);
-      g_wall_fix<S, R>(g, fin, N, own, z, nz, rho0, Td, Tu, lam);
-      R rho, jx, jy, jz;
-      density_momentum<R>(f, rho, jx, jy, jz);
-      R E = g[0];
+      const unsigned own = (unsigned)z * plane + (unsigned)(crow[1] + ccol[1]);
+      const int t = ty * BX + tx;
+      const bool wallz = (z == 0 || z == nz - 1);
+      S gr[Q];
+      if (wallz) pull_raw<S, true>(gr, gin, N, z, nz, plane, ccol, crow);
+      else pull_raw<S, false>(gr, gin, N, z, nz, plane, ccol, crow);
+      R g[Q];
 #pragma unroll
-      for (int l = 1; l < Q; ++l) E = E + g[l];
-      const R T = E / rho;
-      const R* u0 = u_s + slot3(z) * 3 * HXY;
+      for (int l = 0; l < Q; ++l) g[l] = cvt<S, R>(gr[l]);
+      if (wallz) g_wall_fix<S, R>(g, fin, (int)N, (int)own, z, nz, rho0, T0, Td, Tu, lam);
+      const S* fc = fc_s + slot3(z) * Q * TXY + t;
+      R f[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fc[l * TXY]);
       const int cc = (ty + 1) * HX + (tx + 1);
+      const R* rjc = rj_s + slot3(z) * 5 * HXY + cc;
+      const R rho = rjc[0], inv = rjc[HXY];
+      const R jx = rjc[2 * HXY], jy = rjc[3 * HXY], jz = rjc[4 * HXY];
+      const R drho = rho - rho0;
+      R dE = g[0];
+#pragma unroll
+      for (int l = 1; l < Q; ++l) dE = dE + g[l];
+      const R E = E0 + dE;          // rho T
+      const R T = E * inv;
+      const R* u0 = u_s + slot3(z) * 3 * HXY;
       const R ux = u0[cc], uy = u0[HXY + cc], uz = u0[2 * HXY + cc];
       if constexpr (MODE == MODE_STEP) {
-        const int t = ty * BX + tx;
         const R* Fs = F_s + slot2(z) * 3 * TXY;
         const R Fx = Fs[t], Fy = Fs[TXY + t], Fz = Fs[2 * TXY + t];
         const R* um = u_s + slot3(z - 1) * 3 * HXY;
@@ -348,32 +408,51 @@ lb_fused_kernel(const KArgs a) {
         R D = R(0.5) * (u0[cc + 1] - u0[cc - 1]);
         D = D + R(0.5) * (u0[HXY + cc + HX] - u0[HXY + cc - HX]);
         D = D + R(0.5) * (uzp - uzm);
-        // f collision with the shifted velocity u' = (j + tau F)/rho and T in f^eq
-        const R tau = R(a.tau_nu), om = R(a.omega_nu), omk = R(a.omega_kappa);
-        const R vx = (jx + tau * Fx) / rho, vy = (jy + tau * Fy) / rho, vz = (jz + tau * Fz) / rho;
-        const R vv = vx * vx + vy * vy + vz * vz;
-        const R th = R(4.5) * (T - R(1) / R(3));
         S* __restrict__ fo = static_cast<S*>(a.fout);
         S* __restrict__ go = static_cast<S*>(a.gout);
+        // f: BGK towards f^eq(rho, u', T), u' = (j + tau F)/rho. f^eq - fbase per class:
+        // w [drho - 1.5 rho v.v + 4.5 (|c|^2-1)(dE - drho/3) + 3 rho c.v + 4.5 rho (c.v)^2]
+        // (rho (T - 1/3) - rho0 (T0 - 1/3) = dE - drho/3 since rho T = E).
+        {
+          const R tau = R(a.tau_nu), om = R(a.omega_nu), om1 = R(1) - om;
+          const R vx = (jx + tau * Fx) * inv, vy = (jy + tau * Fy) * inv, vz = (jz + tau * Fz) * inv;
+          const R a0 = drho - R(1.5) * rho * (vx * vx + vy * vy + vz * vz);
+          const R th = R(4.5) * (dE - drho * R(1.0 / 3.0));
+          const R A[3] = {a0 - th, a0, a0 + th};
+          const R r3 = R(3) * rho, r45 = R(4.5) * rho;
 #pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
-          const R feq = WT<R>(l) * rho *
-              (R(1) + R(3) * cv + R(4.5) * cv * cv - R(1.5) * vv + th * R(CSQ(l) - 1));
-          Store<S>::st(fo + (size_t)l * N + own, f[l] + (feq - f[l]) * om, WT<R>(l) * rho0);
+          for (int l = 0; l < Q; ++l) {
+            if (l != 0 && (l & 1) == 0) continue;     // handled with its odd partner
+            const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
+            const R w = WT<R>(l) * om;
+            const R sym = A[CLS(l)] + r45 * cv * cv;
+            const R asym = r3 * cv;
+            Store<S>::st(fo + ((unsigned)l * N + own), om1 * f[l] + w * (sym + asym));
+            if (l != 0) Store<S>::st(fo + ((unsigned)OPP(l) * N + own), om1 * f[OPP(l)] + w * (sym - asym));
+          }
         }
-        // g collision with the physical velocity and the counter term S = -rho T div(u)/c_v
-        const R uu = ux * ux + uy * uy + uz * uz;
-        const R Erho = rho * T;
-        const R Ssrc = -Erho * D * R(a.inv_cv);
-        const R lt = R(4.5) * (lam * T - Erho / R(3));
+        // g: BGK towards g^eq(rho, T, u) plus the counter term w_l S, S = -rho T div(u)/c_v.
+        // g^eq - gbase per class: w [dE - 1.5 E u.u + 4.5 (|c|^2-1)(lam (T-T0) - dE/3) + 3 E c.u
+        // + 4.5 E (c.u)^2], T - T0 = (dE - T0 drho)/rho.
+        {
+          const R omk = R(a.omega_kappa), omk1 = R(1) - omk;
+          const R Ssrc = -E * D * R(a.inv_cv);
+          const R b0 = dE - R(1.5) * E * (ux * ux + uy * uy + uz * uz);
+          const R tg = R(4.5) * (lam * ((dE - T0 * drho) * inv) - dE * R(1.0 / 3.0));
+          const R B[3] = {b0 - tg, b0, b0 + tg};
+          const R e3 = R(3) * E, e45 = R(4.5) * E;
 #pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          const R cu = R(CX(l)) * ux + R(CY(l)) * uy + R(CZ(l)) * uz;
-          const R geq = WT<R>(l) * (Erho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu)
-                                    + lt * R(CSQ(l) - 1));
-          Store<S>::st(go + (size_t)l * N + own, g[l] + (geq - g[l]) * omk + WT<R>(l) * Ssrc,
-                       WT<R>(l) * E0);
+          for (int l = 0; l < Q; ++l) {
+            if (l != 0 && (l & 1) == 0) continue;
+            const R cu = R(CX(l)) * ux + R(CY(l)) * uy + R(CZ(l)) * uz;
+            const R w = WT<R>(l);
+            const R sym = B[CLS(l)] + e45 * cu * cu;
+            const R asym = e3 * cu;
+            const R src = w * Ssrc;
+            Store<S>::st(go + ((unsigned)l * N + own), omk1 * g[l] + (w * omk) * (sym + asym) + src);
+            if (l != 0)
+              Store<S>::st(go + ((unsigned)OPP(l) * N + own), omk1 * g[OPP(l)] + (w * omk) * (sym - asym) + src);
+          }
         }
       } else {
         if (a.rho_out) a.rho_out[own] = double(rho);
@@ -381,10 +460,10 @@ lb_fused_kernel(const KArgs a) {
         if (a.uy_out) a.uy_out[own] = double(uy);
         if (a.uz_out) a.uz_out[own] = double(uz);
         if (a.T_out) a.T_out[own] = double(T);
-        const double drho = double(rho), dT = double(T), duz = double(uz);
-        const double U = a.c_v * dT + 0.25 * a.G * exp(-2.0 / drho);
-        d_conv = drho * U * duz; d_T = dT; d_rho = drho; d_E = drho * dT; d_mr = drho; d_mT = dT;
-        d_bad = (isfinite(drho) && isfinite(dT) && isfinite(double(ux)) && isfinite(double(uy)) &&
+        const double drho_ = double(rho), dT = double(T), duz = double(uz);
+        const double U = a.c_v * dT + 0.25 * a.G * exp(-2.0 / drho_);
+        d_conv = drho_ * U * duz; d_T = dT; d_rho = drho_; d_E = double(E); d_mr = drho_; d_mT = dT;
+        d_bad = (isfinite(drho_) && isfinite(dT) && isfinite(double(ux)) && isfinite(double(uy)) &&
                  isfinite(duz)) ? 0.0 : 1.0;
       }
     }
@@ -411,17 +490,18 @@ lb_fused_kernel(const KArgs a) {
           for (int k = 0; k < 7; ++k) out[k] = acc[k];
           out[7] = 0.0;
         }
-        __syncthreads();
       }
     }
+    // the next M stage refills the ring slots that this C stage read
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // Initial state: buffer B0 whose pull gives f = f^eq(rho, 0, T), g = g^eq(rho, T, 0).
-// B0_l(y) = eq_l(y + c_l) where y + c_l is inside, else the wall slot pulled back by the
-// bounce-back of opp(l) at y: f-slot = f^eq_{opp(l)}(y); g-slot chosen so that the thermal
-// wall rule returns g^eq_{opp(l)}(y) with rho_prev = sum_m B0f_m(y) (as stored).
+// B0_l(y) = eq_l(y + c_l) where y + c_l is inside, else the wall slot that the bounce-back of
+// opp(l) at y pulls: f-slot = f^eq_{opp(l)}(y); g-slot chosen so that the thermal wall rule
+// returns g^eq_{opp(l)}(y) with rho_p = the sum of the stored f-slots of y. Stored as deviations.
 // ---------------------------------------------------------------------------------------
 template <class S>
 __global__ void lb_init_kernel(const KArgs a, const double* __restrict__ rho_in,
@@ -430,40 +510,39 @@ __global__ void lb_init_kernel(const KArgs a, const double* __restrict__ rho_in,
   S* __restrict__ fo = static_cast<S*>(a.fout);
   S* __restrict__ go = static_cast<S*>(a.gout);
   const int nx = a.nx, ny = a.ny, nz = a.nz, plane = a.plane, N = a.N;
-  const R rho0 = R(a.rho0), E0 = R(a.E0), lam = R(a.lam);
+  const R rho0 = R(a.rho0), E0 = R(a.E0), T0 = R(a.T0), lam = R(a.lam);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
     const int x = idx % nx, y = (idx / nx) % ny, z = idx / plane;
     R fb[Q];
-    bool wall[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       const int zn = z + CZ(l);
-      wall[l] = (zn < 0 || zn >= nz);
-      const int src = wall[l] ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
-      const int le = wall[l] ? OPP(l) : l;   // equilibrium direction stored in this slot
+      const bool wall = (zn < 0 || zn >= nz);
+      const int src = wall ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
+      const int le = wall ? OPP(l) : l;   // direction whose equilibrium this slot carries
       const R r = R(rho_in[src]), T = R(T_in[src]);
-      const R feq = WT<R>(le) * r * (R(1) + R(4.5) * (T - R(1) / R(3)) * R(CSQ(le) - 1));
-      Store<S>::st(fo + (size_t)l * N + idx, feq, WT<R>(l) * rho0);
-      fb[l] = Store<S>::rt(feq, WT<R>(l) * rho0);   // the value a later load returns
+      const R drho = r - rho0, dE = r * T - E0;
+      const R df = WT<R>(le) * (drho + R(4.5) * (dE - drho / R(3)) * R(CSQ(le) - 1));
+      Store<S>::st(fo + (size_t)l * N + idx, df);
+      fb[l] = Store<S>::rt(df);   // the value a later load returns
     }
-    // rho_prev exactly as the step kernel forms it from the stored values
-    R rp = fb[0];
+    R dp = fb[0];                 // rho_p - rho0 as the step kernel forms it
 #pragma unroll
-    for (int m = 1; m < Q; ++m) rp = rp + fb[m];
+    for (int m = 1; m < Q; ++m) dp = dp + fb[m];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       const int zn = z + CZ(l);
-      const int src = wall[l] ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
-      const int le = wall[l] ? OPP(l) : l;
+      const bool wall = (zn < 0 || zn >= nz);
+      const int src = wall ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
+      const int le = wall ? OPP(l) : l;
       const R r = R(rho_in[src]), T = R(T_in[src]);
-      const R E = r * T;
-      R geq = WT<R>(le) * (E + R(4.5) * (lam * T - E / R(3)) * R(CSQ(le) - 1));
-      if (wall[l]) {
-        // slot l at y is pulled by direction le = opp(l), arriving through the wall at y
+      const R dE = r * T - E0;
+      R dg = WT<R>(le) * (dE + R(4.5) * (lam * (T - T0) - dE / R(3)) * R(CSQ(le) - 1));
+      if (wall) {
         const R Tw = (CZ(le) > 0) ? R(a.T_d) : R(a.T_u);
-        geq = R(2) * wall_even<R>(le, rp, Tw, lam) - geq;
+        dg = R(2) * wall_even_dev<R>(le, dp, rho0, T0, Tw, lam) - dg;
       }
-      Store<S>::st(go + (size_t)l * N + idx, geq, WT<R>(l) * E0);
+      Store<S>::st(go + (size_t)l * N + idx, dg);
     }
   }
 }
@@ -480,13 +559,13 @@ __global__ void lb_pops_kernel(const KArgs a, double* __restrict__ fo, double* _
     int col[3], row[3];
     for (int j = 0; j < 3; ++j) { col[j] = wrapi(x - 1 + j, nx); row[j] = wrapi(y - 1 + j, ny) * nx; }
     R f[Q], g[Q];
-    pull<S, R>(f, fin, N, z, nz, plane, col, row, R(a.rho0));
-    pull<S, R>(g, gin, N, z, nz, plane, col, row, R(a.E0));
-    g_wall_fix<S, R>(g, fin, N, idx, z, nz, R(a.rho0), R(a.T_d), R(a.T_u), R(a.lam));
+    pull<S, R>(f, fin, N, z, nz, plane, col, row);
+    pull<S, R>(g, gin, N, z, nz, plane, col, row);
+    g_wall_fix<S, R>(g, fin, N, idx, z, nz, R(a.rho0), R(a.T0), R(a.T_d), R(a.T_u), R(a.lam));
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      if (fo) fo[(size_t)l * N + idx] = double(f[l]);
-      if (go) go[(size_t)l * N + idx] = double(g[l]);
+      if (fo) fo[(size_t)l * N + idx] = double(f[l]) + a.fbase[CSQ(l)];
+      if (go) go[(size_t)l * N + idx] = double(g[l]) + a.gbase[CSQ(l)];
     }
   }
 }

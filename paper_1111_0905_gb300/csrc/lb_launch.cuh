@@ -12,6 +12,7 @@ struct PrecOps {
   cudaError_t (*fused)(const KArgs&, int mode, int by, dim3 grid, cudaStream_t);
   cudaError_t (*init)(const KArgs&, const double*, const double*, cudaStream_t);
   cudaError_t (*pops)(const KArgs&, double*, double*, cudaStream_t);
+  bool (*tile_ok)(int by);    // whether the tile height's shared-memory window fits a CTA
 };
 
 extern const PrecOps kOpsF64, kOpsF32, kOpsBF16, kOpsF16;
@@ -19,10 +20,17 @@ extern const PrecOps kOpsF64, kOpsF32, kOpsBF16, kOpsF16;
 template <class S> struct OpsImpl {
   using R = typename Store<S>::R;
 
+  // dynamic shared memory of a tile height; tile heights whose windows exceed the 227 KB a CTA
+  // may use are not available (FP64 with BY = 16)
+  template <int BY> static constexpr size_t smem() { return Geo<BY>::template smem_bytes<S, R>(); }
+  template <int BY> static constexpr bool fits() { return smem<BY>() + 1024 <= 227u * 1024u; }
   template <int BY, int MODE> static cudaError_t attr() {
-    return cudaFuncSetAttribute(lb_fused_kernel<S, BY, MODE>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Geo<BY>::template smem_bytes<R>());
+    if constexpr (!fits<BY>()) {
+      return cudaSuccess;
+    } else {
+      return cudaFuncSetAttribute(lb_fused_kernel<S, BY, MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem<BY>());
+    }
   }
   static cudaError_t prepare() {
     cudaError_t e;
@@ -33,10 +41,16 @@ template <class S> struct OpsImpl {
     if ((e = attr<8, MODE_MOMENTS>()) != cudaSuccess) return e;
     return attr<16, MODE_MOMENTS>();
   }
+  static bool tile_ok(int by) {
+    return (by == 4 && fits<4>()) || (by == 8 && fits<8>()) || (by == 16 && fits<16>());
+  }
   template <int BY, int MODE> static cudaError_t go(const KArgs& a, dim3 grid, cudaStream_t st) {
-    lb_fused_kernel<S, BY, MODE>
-        <<<grid, dim3(BX, BY), Geo<BY>::template smem_bytes<R>(), st>>>(a);
-    return cudaGetLastError();
+    if constexpr (!fits<BY>()) {
+      return cudaErrorInvalidConfiguration;
+    } else {
+      lb_fused_kernel<S, BY, MODE><<<grid, dim3(BX, BY), smem<BY>(), st>>>(a);
+      return cudaGetLastError();
+    }
   }
   static cudaError_t fused(const KArgs& a, int mode, int by, dim3 grid, cudaStream_t st) {
     if (mode == MODE_STEP) {

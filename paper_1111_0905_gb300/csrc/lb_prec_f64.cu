@@ -3,5 +3,6 @@
 
 namespace tlbm {
 const PrecOps kOpsF64 = {sizeof(double), 0, &OpsImpl<double>::prepare, &OpsImpl<double>::fused,
-                    &OpsImpl<double>::init, &OpsImpl<double>::pops};
+                    &OpsImpl<double>::init, &OpsImpl<double>::pops,
+                    &OpsImpl<double>::tile_ok};
 }  // namespace tlbm
