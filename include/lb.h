@@ -46,9 +46,11 @@ extern "C" {
 typedef enum {
   LB_FP64 = 0,     /* float64 storage and compute */
   LB_FP32 = 1,     /* float32 storage and compute */
-  LB_BF16_DEV = 2, /* bfloat16 storage of f_l - w_l rho0 and g_l - w_l rho0 T0, float32 compute */
-  LB_FP16_DEV = 3  /* float16 storage of the same deviations, float32 compute */
+  LB_BF16_DEV = 2, /* bfloat16 storage of the deviations below, float32 compute */
+  LB_FP16_DEV = 3  /* float16 storage of the deviations below, float32 compute */
 } lb_precision;
+/* Every precision stores deviations from the reference equilibria, f_l - f^eq_l(rho0, 0, T0) and
+ * g_l - g^eq_l(rho0, T0, 0), and forms moments and equilibria from them. */
 
 typedef struct {
   int nx, ny, nz;         /* grid; each >= 1, 19*nx*ny*nz < 2^32 */
@@ -59,7 +61,7 @@ typedef struct {
   double c_v;             /* specific heat at constant volume, Eq. (3); > 0 (1 = default) */
   double g_z;             /* signed gravity along z, Eq. (1) (negative = downward) */
   double T_d, T_u;        /* bottom / top wall temperatures */
-  double rho0, T0;        /* reference state of the 16-bit deviation storage; <= 0: mean of init */
+  double rho0, T0;        /* reference state of the deviation storage; <= 0: mean of the init fields */
   int precision;          /* lb_precision */
   int nu_every;           /* > 0: accumulate Nu_mean every nu_every steps into the time average */
   int check_every;        /* > 0: lb_step checks rho > 0, T > 0, no NaN every check_every steps */
@@ -132,6 +134,28 @@ const char* lb_strerror(int code);
 
 /* lb_last_error -- the context's last error message ("" if none); a static message if ctx is NULL. */
 const char* lb_last_error(const lb_ctx* ctx);
+
+/* lb_nusselt_fields_noalloc -- Nu(z) of lb_nusselt computed from caller-owned device fields, for
+ * callers that cannot allocate device memory (an application whose own pool allocator owns all
+ * device memory, or a latency-critical loop that cannot take cudaMalloc's implicit
+ * synchronisation). The paper has no counterpart; it is a variant of the Nusselt reduction of
+ * the diagnostics path. It allocates nothing: its per-plane partial sums live in a fixed
+ * file-scope device array of 2 * LB_NOALLOC_MAX_NZ doubles (128 KB) that every GPU loading the
+ * library keeps until the process exits.
+ * Inputs (device, float64, node-index order, nx*ny*nz each): rho, uz (physical velocity, z),
+ * T, e.g. written by lb_moments with on_device = 1. Output (device, float64): nu_out[0..nz-1] =
+ * Nu(z), nu_out[nz] = mean over z. Parameters as in lb_params. Enqueued on cuda_stream
+ * (NULL = legacy default stream) of the current device; nothing is synchronised.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it; make that first call before any stream capture. Every call shares the array:
+ * calls that overlap on the GPU (other streams, other threads) race and must be ordered by the
+ * caller. Each call writes every partial it reads, so no state carries over between calls.
+ * Errors: LB_EINVAL (null pointer, nx/ny/nz < 1, nz > LB_NOALLOC_MAX_NZ, kappa <= 0, c_v <= 0,
+ * T_d == T_u), LB_ECUDA (symbol lookup or launch failed). */
+#define LB_NOALLOC_MAX_NZ 8192
+int lb_nusselt_fields_noalloc(const double* rho, const double* uz, const double* T,
+                              int nx, int ny, int nz, double kappa, double G, double c_v,
+                              double T_d, double T_u, double* nu_out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,9 @@ _lib = None
 
 # Names declared in include/lb.h.
 EXPORTS = ("lb_init", "lb_step", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
-           "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error")
+           "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error",
+           "lb_nusselt_fields_noalloc")
+NOALLOC_MAX_NZ = 8192
 
 
 class LbParams(ctypes.Structure):
@@ -112,6 +114,8 @@ def load_library():
     lib.lb_strerror.restype = ctypes.c_char_p
     lib.lb_last_error.argtypes = [P]
     lib.lb_last_error.restype = ctypes.c_char_p
+    lib.lb_nusselt_fields_noalloc.argtypes = [P, P, P, I, I, I, D, D, D, D, D, P, P]
+    lib.lb_nusselt_fields_noalloc.restype = I
     _lib = lib
     return lib
 
@@ -140,6 +144,18 @@ def _current_stream():
     except ImportError:  # pragma: no cover
         pass
     return None
+
+
+def nusselt_fields_noalloc(params: Params, rho, uz, T, nu_out, stream=None) -> None:
+    """lb_nusselt_fields_noalloc on CUDA tensors (inputs [nz, ny, nx] float64; nu_out nz + 1
+    float64); enqueued on the current stream, allocates no device memory."""
+    lib = load_library()
+    st = _current_stream() if stream is None else stream
+    rc = lib.lb_nusselt_fields_noalloc(_ptr(rho), _ptr(uz), _ptr(T), params.nx, params.ny, params.nz,
+                                       params.kappa, params.G, params.c_v, params.T_d, params.T_u,
+                                       _ptr(nu_out), st)
+    if rc != 0:
+        raise LBError(rc, "lb_nusselt_fields_noalloc", lib.lb_strerror(rc).decode())
 
 
 class Lattice:
