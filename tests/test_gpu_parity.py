@@ -26,15 +26,18 @@ def _gpu_run(p, rho, T, steps):
     return lat, rho_g, u_g, T_g, f_g, g_g, nu
 
 
-def _compare(p, rho, T, steps, tol, nu_tol=None, pops=True):
+def _compare(p, rho, T, steps, tol, nu_tol=None, pops=True, u_floor=None):
     lat, rho_g, u_g, T_g, f_g, g_g, nu = _gpu_run(p, rho, T, steps)
     f, g, op, _ = oracle_run(p, rho, T, steps)
     r_o, u_o, T_o = lbm.moments_out(f, g, op)
     errs = {"rho": rel_err(rho_g, r_o), "T": rel_err(T_g, T_o)}
-    # velocity errors on the velocity scale, floored at 1e-3 lattice units: u = (j + F/2)/rho is
-    # a difference of O(rho) population sums, so its rounding error is absolute (~eps), and a
-    # relative comparison is only meaningful for velocities above ~1e-3 (0.2 % of c_s)
-    u_scale = max(max(float(np.abs(u_o[a].numpy()).max()) for a in range(3)), 1e-3)
+    # velocity errors on the velocity scale with a floor: u = (j + F/2)/rho is a difference of
+    # O(rho) population sums and of the O(0.1)-term force sum of Eq. (9), so its rounding error is
+    # absolute (~1e-16 in FP64, ~1e-8 in FP32). Floors: 1e-3 lattice units for FP64, 1e-2 (Mach
+    # ~0.02, a typical convection velocity) for the FP32/16-bit forms.
+    if u_floor is None:
+        u_floor = 1e-3 if p.precision == lb.LB_FP64 else 1e-2
+    u_scale = max(max(float(np.abs(u_o[a].numpy()).max()) for a in range(3)), u_floor)
     for a in range(3):
         errs[f"u{a}"] = float(np.abs(u_g[a] - u_o[a].numpy()).max()) / u_scale
     if pops:
