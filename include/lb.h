@@ -106,6 +106,22 @@ int lb_moments(lb_ctx* ctx, double* rho, double* ux, double* uy, double* uz, dou
  * FP64 warp-shuffle reductions on the device; synchronises. Errors: LB_EINVAL, LB_ECUDA. */
 int lb_nusselt(lb_ctx* ctx, double* nu_mean, double* nu_z, double* nu_time_avg);
 
+/* lb_adjoint_step -- advance nsteps steps from the current state (as lb_step) and return the
+ * time-averaged Nusselt number J = (1/nsteps) sum_{n=1..nsteps} Nu_mean(state n) (Eq. (4)) with its
+ * exact discrete gradient by reverse mode: dJ/dT_d, dJ/dT_u, dJ/dG and, if dJ_dT0 is not NULL,
+ * dJ/dT0 (host float64 [nx*ny*nz]) with respect to the temperature field passed to lb_init (then
+ * the context must be at step 0). The paper defines no adjoint; the reverse pass transposes the
+ * operations of lb_step (streaming and wall rules, f and g collisions with the counter term, the
+ * velocities and divergence, the force of Eq. (9) with psi = exp(-1/rho), the moments of Eq. (8))
+ * in FP64 around the forward states of the context's precision, which are recomputed segment by
+ * segment from checkpoints taken every checkpoint_every steps. Output pointers may be NULL.
+ * Device memory: nsteps/checkpoint_every + 1 population checkpoints, checkpoint_every + 1 float64
+ * states, 2 float64 adjoint states and ~35 float64 fields, allocated and freed by the call.
+ * Synchronises. Errors: LB_EINVAL (nsteps < 1, checkpoint_every < 1, T_d == T_u, dJ_dT0 requested
+ * after lb_step), LB_ENOMEM, LB_ECUDA. */
+int lb_adjoint_step(lb_ctx* ctx, long long nsteps, int checkpoint_every, double* J,
+                    double* dJ_dTd, double* dJ_dTu, double* dJ_dG, double* dJ_dT0);
+
 /* lb_populations -- the current pre-collision state (f_l, g_l) as float64 [19][nx*ny*nz] each
  * (Eqs. (6)-(7): populations after streaming). Host memory if on_device == 0. Either pointer
  * may be NULL. Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */

@@ -324,3 +324,21 @@ def moments_out(f, g, p: Params):
     """rho, (u_x, u_y, u_z) physical, T of the state, as exported by lb_moments."""
     rho, j, T, F, u_eq, u = macroscopic(f, g, p)
     return rho, u, T
+
+
+# ---------------------------------------------------------------------------------------
+# Objective of the adjoint: time-averaged Nusselt number.
+# ---------------------------------------------------------------------------------------
+
+def time_averaged_nusselt(rho0, T0, p: Params, nsteps: int):
+    """J = (1/N) sum_{n=1..N} Nu_mean(state n), starting from the equilibrium of (rho0, T0).
+
+    Differentiable (PyTorch autograd) in T0 and in p.T_d, p.T_u, p.G when those are tensors:
+    the reverse pass of autograd through these plain steps is the exact discrete gradient.
+    """
+    f, g = init_state(rho0, T0, p)
+    J = 0.0
+    for _ in range(nsteps):
+        f, g = step(f, g, p)
+        J = J + nusselt(f, g, p)[0]
+    return J / nsteps

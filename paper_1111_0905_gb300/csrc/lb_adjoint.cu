@@ -1,0 +1,446 @@
+// lb_adjoint.cu -- discrete adjoint of the thermal D3Q19 step (reverse mode, FP64).
+//
+// Objective: J = (1/N) sum_{n=1..N} Nu_mean(x_n), the time-averaged Nusselt number of Eq. (4),
+// x_n the pre-collision state at step n, x_{n+1} = Phi(x_n) the step of Eqs. (6)-(9) with the
+// readings of the forward kernels. Gradients: dJ/dT_d, dJ/dT_u, dJ/dG and dJ/dT0 (the initial
+// temperature field of lb_init). The adjoint state lambda_n = dJ/dx_n obeys
+//   lambda_N = (1/N) dNu/dx_N,  lambda_n = (dPhi/dx_n)^T lambda_{n+1} + [n >= 1] (1/N) dNu/dx_n.
+// One reverse step, for state n, in the reverse order of the forward operations:
+//   streaming^T (push of lambda_{n+1}, bounce-back transposed, the thermal wall rule's density
+//   and T_w terms) -> collision^T (f^eq(rho, u', T), g^eq(rho, T, u), counter term) -> the Nu
+//   terms of state n -> divergence^T (radius-1 gather) -> velocities^T (u, u' -> j, F, rho) ->
+//   force^T (radius-1 psi gather with the mirrored wall ghosts; dJ/dG) -> moments^T.
+// The forward states are recomputed per segment from checkpoints taken every K steps; the
+// macroscopic fields of a state are recomputed per reverse step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lb_ctx.h"
+
+namespace tlbm {
+namespace adj {
+
+struct Geom { int nx, ny, nz, plane, N; };
+struct Par {
+  double tau, om, omk, G, gz, lam, cv, kappa, Td, Tu;
+  double Kc;        // 1 / (N_t kappa (T_d - T_u) nx ny): weight of sum_x rho U u_z in J
+  int include_nu;   // add (1/N_t) dNu_mean/dx of this state
+};
+
+// fields of M (recomputed forward macros of one state), each [N]
+enum { MF_RHO = 0, MF_JX, MF_JY, MF_JZ, MF_E, MF_T, MF_PSI, MF_FX, MF_FY, MF_FZ, MF_UX, MF_UY, MF_UZ,
+       MF_VX, MF_VY, MF_VZ, MF_D, MF_AX, MF_AY, MF_AZ, MF_COUNT };
+// fields of A (adjoints of the macros), each [N]
+enum { AF_RHO = 0, AF_T, AF_UX, AF_UY, AF_UZ, AF_VX, AF_VY, AF_VZ, AF_D, AF_FX, AF_FY, AF_FZ, AF_JX, AF_JY,
+       AF_JZ, AF_COUNT };
+// per-block parameter partials
+enum { P_TD = 0, P_TU, P_G, P_COUNT };
+
+constexpr int kBlocks = 1024;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void coords(int idx, const Geom& g, int& x, int& y, int& z) {
+  x = idx % g.nx;
+  y = (idx / g.nx) % g.ny;
+  z = idx / g.plane;
+}
+__device__ __forceinline__ int at(const Geom& g, int x, int y, int z) {
+  return z * g.plane + wrapi(y, g.ny) * g.nx + wrapi(x, g.nx);
+}
+
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+  return s;
+}
+
+// rho, j, E, T, psi of state X ([38][N]: f then g, pre-collision, float64)
+__global__ void macro_kernel(const double* __restrict__ X, Geom g, double* __restrict__ M) {
+  const size_t N = g.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+    double f[Q], E = 0.0;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) f[l] = X[l * N + i];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) E += X[(Q + l) * N + i];
+    double rho, jx, jy, jz;
+    density_momentum<double>(f, rho, jx, jy, jz);
+    M[MF_RHO * N + i] = rho; M[MF_JX * N + i] = jx; M[MF_JY * N + i] = jy; M[MF_JZ * N + i] = jz;
+    M[MF_E * N + i] = E; M[MF_T * N + i] = E / rho; M[MF_PSI * N + i] = exp(-1.0 / rho);
+  }
+}
+
+// Eq. (9): A_a = sum_{l>=1} W_l c_la psi(x + c_l) (mirrored ghosts), F = -G psi A + rho g_z z,
+// u = (j + F/2)/rho, u' = (j + tau F)/rho
+__global__ void force_fwd_kernel(Geom g, Par p, double* __restrict__ M) {
+  const size_t N = g.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(i, g, x, y, z);
+    double A[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int l = 1; l < Q; ++l) {
+      const double nb = M[MF_PSI * N + at(g, x + CX(l), y + CY(l), mirror_z(z + CZ(l), g.nz))];
+      if (CX(l)) A[0] += FW<double>(l) * CX(l) * nb;
+      if (CY(l)) A[1] += FW<double>(l) * CY(l) * nb;
+      if (CZ(l)) A[2] += FW<double>(l) * CZ(l) * nb;
+    }
+    const double rho = M[MF_RHO * N + i], psi = M[MF_PSI * N + i];
+    const double F[3] = {-p.G * psi * A[0], -p.G * psi * A[1], -p.G * psi * A[2] + rho * p.gz};
+    for (int a = 0; a < 3; ++a) {
+      const double j = M[(MF_JX + a) * N + i];
+      M[(MF_AX + a) * N + i] = A[a];
+      M[(MF_FX + a) * N + i] = F[a];
+      M[(MF_UX + a) * N + i] = (j + 0.5 * F[a]) / rho;
+      M[(MF_VX + a) * N + i] = (j + p.tau * F[a]) / rho;
+    }
+  }
+}
+
+// D = sum_a [u_a(x+e_a) - u_a(x-e_a)]/2, u_z -> -u_z across the walls
+__global__ void div_fwd_kernel(Geom g, double* __restrict__ M) {
+  const size_t N = g.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(i, g, x, y, z);
+    const double uz0 = M[MF_UZ * N + i];
+    const double uzp = (z + 1 < g.nz) ? M[MF_UZ * N + i + g.plane] : -uz0;
+    const double uzm = (z - 1 >= 0) ? M[MF_UZ * N + i - g.plane] : -uz0;
+    double D = 0.5 * (M[MF_UX * N + at(g, x + 1, y, z)] - M[MF_UX * N + at(g, x - 1, y, z)]);
+    D += 0.5 * (M[MF_UY * N + at(g, x, y + 1, z)] - M[MF_UY * N + at(g, x, y - 1, z)]);
+    D += 0.5 * (uzp - uzm);
+    M[MF_D * N + i] = D;
+  }
+}
+
+// streaming^T, wall rules^T, collision^T and the Nu terms, per node
+__global__ void coll_adj_kernel(const double* __restrict__ X, const double* __restrict__ M,
+                                const double* __restrict__ Ln, Geom g, Par p,
+                                double* __restrict__ L, double* __restrict__ A,
+                                double* __restrict__ part) {
+  __shared__ double sh[32];
+  const size_t N = g.N;
+  double pTd = 0.0, pTu = 0.0, pG = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(i, g, x, y, z);
+    const double rho = M[MF_RHO * N + i], T = M[MF_T * N + i], E = rho * T;
+    const double ux = M[MF_UX * N + i], uy = M[MF_UY * N + i], uz = M[MF_UZ * N + i];
+    const double vx = M[MF_VX * N + i], vy = M[MF_VY * N + i], vz = M[MF_VZ * N + i];
+    const double D = M[MF_D * N + i];
+    // adjoint of the post-collision populations: lambda*_l(x) = lambda'_l(x + c_l), or through a
+    // wall: the bounce-back that delivered f*_l(x) as f'_{opp(l)}(x) (g: with a minus sign)
+    double lf[Q], lg[Q];
+    double a_rho = 0.0;
+    if (Ln) {
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const int zn = z + CZ(l);
+        if (zn < 0 || zn >= g.nz) {
+          lf[l] = Ln[OPP(l) * N + i];
+          lg[l] = -Ln[(Q + OPP(l)) * N + i];
+        } else {
+          const int j = at(g, x + CX(l), y + CY(l), zn);
+          lf[l] = Ln[l * N + j];
+          lg[l] = Ln[(Q + l) * N + j];
+        }
+      }
+      // thermal wall rule: g'_m(x_w) = ... + 2 w_m [rho T_w + 4.5 (lam T_w - rho T_w/3)(|c_m|^2-1)]
+#pragma unroll
+      for (int m = 0; m < Q; ++m) {
+        const bool bot = (CZ(m) > 0 && z == 0), top = (CZ(m) < 0 && z == g.nz - 1);
+        if (bot || top) {
+          const double Tw = bot ? p.Td : p.Tu;
+          const double lm = Ln[(Q + m) * N + i];
+          const double k = CSQ(m) - 1;
+          a_rho += 2.0 * WT<double>(m) * Tw * (1.0 - 1.5 * k) * lm;
+          const double dTw = 2.0 * WT<double>(m) * (rho + 4.5 * (p.lam - rho / 3.0) * k) * lm;
+          if (bot) pTd += dTw; else pTu += dTw;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < Q; ++l) { lf[l] = 0.0; lg[l] = 0.0; }
+    }
+    // collision^T: f* = (1 - om) f + om f^eq(rho, v, T), g* = (1 - omk) g + omk g^eq(rho, T, u) + w S
+    double a_T = 0.0, a_v[3] = {0.0, 0.0, 0.0}, a_u[3] = {0.0, 0.0, 0.0};
+    const double vv = vx * vx + vy * vy + vz * vz, uu = ux * ux + uy * uy + uz * uz;
+    double lS = 0.0;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const double k = CSQ(l) - 1, w = WT<double>(l);
+      const double cv = CX(l) * vx + CY(l) * vy + CZ(l) * vz;
+      const double Qf = 1.0 + 3.0 * cv + 4.5 * cv * cv - 1.5 * vv + 4.5 * (T - 1.0 / 3.0) * k;
+      const double af = p.om * lf[l] * w;
+      a_rho += af * Qf;
+      a_T += af * rho * 4.5 * k;
+      const double dv = af * rho;
+      a_v[0] += dv * (3.0 * CX(l) + 9.0 * cv * CX(l) - 3.0 * vx);
+      a_v[1] += dv * (3.0 * CY(l) + 9.0 * cv * CY(l) - 3.0 * vy);
+      a_v[2] += dv * (3.0 * CZ(l) + 9.0 * cv * CZ(l) - 3.0 * vz);
+      const double cu = CX(l) * ux + CY(l) * uy + CZ(l) * uz;
+      const double Pu = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu;
+      const double ag = p.omk * lg[l] * w;
+      a_rho += ag * T * (Pu - 1.5 * k);
+      a_T += ag * (rho * Pu + 4.5 * (p.lam - rho / 3.0) * k);
+      const double du = ag * E;
+      a_u[0] += du * (3.0 * CX(l) + 9.0 * cu * CX(l) - 3.0 * ux);
+      a_u[1] += du * (3.0 * CY(l) + 9.0 * cu * CY(l) - 3.0 * uy);
+      a_u[2] += du * (3.0 * CZ(l) + 9.0 * cu * CZ(l) - 3.0 * uz);
+      lS += w * lg[l];
+      L[l * N + i] = (1.0 - p.om) * lf[l];
+      L[(Q + l) * N + i] = (1.0 - p.omk) * lg[l];
+    }
+    // counter term S = -rho T D / c_v
+    a_rho += lS * (-T * D / p.cv);
+    a_T += lS * (-rho * D / p.cv);
+    const double a_D = lS * (-E / p.cv);
+    // Nu terms: J_n = (1/N_t)[1 + sum_x rho U u_z / (kappa (T_d - T_u) nx ny)], U = c_v T + (G/4) e^{-2/rho}
+    if (p.include_nu) {
+      const double e2 = exp(-2.0 / rho);
+      const double U = p.cv * T + 0.25 * p.G * e2;
+      a_rho += p.Kc * (U * uz + rho * uz * 0.5 * p.G * e2 / (rho * rho));
+      a_T += p.Kc * rho * p.cv * uz;
+      a_u[2] += p.Kc * rho * U;
+      pG += p.Kc * rho * uz * 0.25 * e2;
+      const double conv = p.Kc * rho * U * uz / (p.Td - p.Tu);
+      pTd -= conv;
+      pTu += conv;
+    }
+    A[AF_RHO * N + i] = a_rho; A[AF_T * N + i] = a_T; A[AF_D * N + i] = a_D;
+    A[AF_UX * N + i] = a_u[0]; A[AF_UY * N + i] = a_u[1]; A[AF_UZ * N + i] = a_u[2];
+    A[AF_VX * N + i] = a_v[0]; A[AF_VY * N + i] = a_v[1]; A[AF_VZ * N + i] = a_v[2];
+  }
+  const double s0 = block_sum(pTd, sh), s1 = block_sum(pTu, sh), s2 = block_sum(pG, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x * P_COUNT + P_TD] += s0;
+    part[blockIdx.x * P_COUNT + P_TU] += s1;
+    part[blockIdx.x * P_COUNT + P_G] += s2;
+  }
+}
+
+// divergence^T (radius-1 gather) and velocities^T: u = (j + F/2)/rho, u' = (j + tau F)/rho
+__global__ void vel_adj_kernel(const double* __restrict__ M, Geom g, Par p, double* __restrict__ A) {
+  const size_t N = g.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(i, g, x, y, z);
+    double lu[3] = {A[AF_UX * N + i], A[AF_UY * N + i], A[AF_UZ * N + i]};
+    lu[0] += 0.5 * (A[AF_D * N + at(g, x - 1, y, z)] - A[AF_D * N + at(g, x + 1, y, z)]);
+    lu[1] += 0.5 * (A[AF_D * N + at(g, x, y - 1, z)] - A[AF_D * N + at(g, x, y + 1, z)]);
+    const double dm = (z >= 1) ? A[AF_D * N + i - g.plane] : A[AF_D * N + i];
+    const double dp = (z <= g.nz - 2) ? A[AF_D * N + i + g.plane] : A[AF_D * N + i];
+    lu[2] += 0.5 * (dm - dp);
+    const double rho = M[MF_RHO * N + i];
+    double a_rho = A[AF_RHO * N + i];
+    for (int a = 0; a < 3; ++a) {
+      const double lv = A[(AF_VX + a) * N + i];
+      A[(AF_JX + a) * N + i] = (lv + lu[a]) / rho;
+      A[(AF_FX + a) * N + i] = (p.tau * lv + 0.5 * lu[a]) / rho;
+      a_rho -= (M[(MF_VX + a) * N + i] * lv + M[(MF_UX + a) * N + i] * lu[a]) / rho;
+    }
+    A[AF_RHO * N + i] = a_rho;
+  }
+}
+
+// force^T (psi gather with mirrored ghosts), psi^T, T = E/rho ^T and moments^T
+__global__ void force_adj_kernel(const double* __restrict__ M, Geom g, Par p,
+                                 const double* __restrict__ A, double* __restrict__ L,
+                                 double* __restrict__ part) {
+  __shared__ double sh[32];
+  const size_t N = g.N;
+  double pG = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(i, g, x, y, z);
+    const double psi = M[MF_PSI * N + i], rho = M[MF_RHO * N + i], T = M[MF_T * N + i];
+    const double lF[3] = {A[AF_FX * N + i], A[AF_FY * N + i], A[AF_FZ * N + i]};
+    // own psi factor of F(x) = -G psi(x) A(x)
+    double lpsi = -p.G * (lF[0] * M[MF_AX * N + i] + lF[1] * M[MF_AY * N + i] + lF[2] * M[MF_AZ * N + i]);
+    pG -= psi * (lF[0] * M[MF_AX * N + i] + lF[1] * M[MF_AY * N + i] + lF[2] * M[MF_AZ * N + i]);
+    // psi(y) enters F(x) for every (x, l) with mirror(x + c_l) = y
+#pragma unroll
+    for (int l = 1; l < Q; ++l) {
+      const double W = FW<double>(l);
+      const int zi = z - CZ(l);          // interior link x = y - c_l
+      if (zi >= 0 && zi < g.nz) {
+        const int j = at(g, x - CX(l), y - CY(l), zi);
+        const double cl = CX(l) * A[AF_FX * N + j] + CY(l) * A[AF_FY * N + j] + CZ(l) * A[AF_FZ * N + j];
+        lpsi += -p.G * W * cl * M[MF_PSI * N + j];
+      }
+      const int zg = z + CZ(l);          // ghost link: x in this plane, x + c_l beyond a wall
+      if (CZ(l) != 0 && (zg < 0 || zg >= g.nz)) {
+        const int j = at(g, x - CX(l), y - CY(l), z);
+        const double cl = CX(l) * A[AF_FX * N + j] + CY(l) * A[AF_FY * N + j] + CZ(l) * A[AF_FZ * N + j];
+        lpsi += -p.G * W * cl * M[MF_PSI * N + j];
+      }
+    }
+    double a_rho = A[AF_RHO * N + i] + p.gz * lF[2] + lpsi * psi / (rho * rho);
+    const double a_T = A[AF_T * N + i];
+    const double a_E = a_T / rho;
+    a_rho -= a_T * T / rho;
+    const double lj[3] = {A[AF_JX * N + i], A[AF_JY * N + i], A[AF_JZ * N + i]};
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      L[l * N + i] += a_rho + CX(l) * lj[0] + CY(l) * lj[1] + CZ(l) * lj[2];
+      L[(Q + l) * N + i] += a_E;
+    }
+  }
+  const double s = block_sum(pG, sh);
+  if (threadIdx.x == 0) part[blockIdx.x * P_COUNT + P_G] += s;
+}
+
+// dJ/dT0 from lambda_0: x_0 = (f^eq(rho0, 0, T0), g^eq(rho0, T0, 0))
+__global__ void init_grad_kernel(const double* __restrict__ L0, const double* __restrict__ X0, Geom g,
+                                 double lam, double* __restrict__ out) {
+  const size_t N = g.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+    double rho = 0.0;
+    for (int l = 0; l < Q; ++l) rho += X0[l * N + i];
+    double s = 0.0;
+    for (int l = 0; l < Q; ++l) {
+      const double k = CSQ(l) - 1, w = WT<double>(l);
+      s += L0[l * N + i] * w * rho * 4.5 * k + L0[(Q + l) * N + i] * w * (rho + 4.5 * (lam - rho / 3.0) * k);
+    }
+    out[i] = s;
+  }
+}
+
+}  // namespace adj
+}  // namespace tlbm
+
+using namespace tlbm;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every, double* J,
+                               double* dJ_dTd, double* dJ_dTu, double* dJ_dG, double* dJ_dT0) {
+  using namespace tlbm::adj;
+  if (!c) return LB_EINVAL;
+  if (nsteps < 1 || checkpoint_every < 1) return lb_fail(c, LB_EINVAL, "nsteps and checkpoint_every must be >= 1");
+  if (dJ_dT0 && c->step != 0) return lb_fail(c, LB_EINVAL, "dJ_dT0 needs the state of lb_init (step 0)");
+  if (!(c->p.T_d != c->p.T_u)) return lb_fail(c, LB_EINVAL, "T_d == T_u: Nu is undefined");
+  const long long K = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+  const long long nck = (nsteps + K - 1) / K;
+  const size_t N = (size_t)c->N;
+  const size_t pbytes = (size_t)Q * N * c->ops->esize;
+  const size_t sbytes = 2 * (size_t)Q * N * sizeof(double);
+  cudaStream_t st = c->stream;
+  Geom g{c->p.nx, c->p.ny, c->p.nz, c->plane, c->N};
+
+  DevBuf ck, rb, xs, mb, ab, lb, pt, acc, d0;
+  if (cudaMalloc(&ck.p, (size_t)nck * 2 * pbytes) != cudaSuccess ||
+      cudaMalloc(&rb.p, 4 * pbytes) != cudaSuccess ||
+      cudaMalloc(&xs.p, (size_t)(K + 1) * sbytes) != cudaSuccess ||
+      cudaMalloc(&mb.p, (size_t)MF_COUNT * N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ab.p, (size_t)AF_COUNT * N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&lb.p, 2 * sbytes) != cudaSuccess ||
+      cudaMalloc(&pt.p, (size_t)kBlocks * P_COUNT * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&acc.p, 2 * sizeof(double)) != cudaSuccess ||
+      (dJ_dT0 && cudaMalloc(&d0.p, N * sizeof(double)) != cudaSuccess))
+    return lb_fail(c, LB_ENOMEM, "adjoint buffers");
+  unsigned char* ckp = static_cast<unsigned char*>(ck.p);
+  unsigned char* rbp = static_cast<unsigned char*>(rb.p);
+  double* Xs = static_cast<double*>(xs.p);
+  double* M = static_cast<double*>(mb.p);
+  double* A = static_cast<double*>(ab.p);
+  double* Lb[2] = {static_cast<double*>(lb.p), static_cast<double*>(lb.p) + 2 * Q * N};
+  double* part = static_cast<double*>(pt.p);
+  double* jacc = static_cast<double*>(acc.p);
+  LB_CU(c, cudaMemsetAsync(part, 0, (size_t)kBlocks * P_COUNT * sizeof(double), st));
+  LB_CU(c, cudaMemsetAsync(jacc, 0, 2 * sizeof(double), st));
+
+  // forward: checkpoints every K steps, J from the Nu of states 1..N
+  const dim3 grid = fused_grid(c);
+  for (long long n = 0; n < nsteps; ++n) {
+    if (n % K == 0) {
+      unsigned char* dst = ckp + (size_t)(n / K) * 2 * pbytes;
+      LB_CU(c, cudaMemcpyAsync(dst, c->f[c->cur], pbytes, cudaMemcpyDeviceToDevice, st));
+      LB_CU(c, cudaMemcpyAsync(dst + pbytes, c->g[c->cur], pbytes, cudaMemcpyDeviceToDevice, st));
+    }
+    KArgs a = make_args(c);
+    LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, st));
+    c->cur ^= 1;
+    c->step += 1;
+    const int rc = run_diag_acc(c, jacc);
+    if (rc != LB_OK) return rc;
+  }
+
+  const double dT = c->p.T_d - c->p.T_u;
+  Par par{c->p.tau_nu, 1.0 / c->p.tau_nu, 1.0 / c->p.tau_kappa, c->p.G, c->p.g_z, c->lam, c->p.c_v,
+          c->p.kappa, c->p.T_d, c->p.T_u,
+          1.0 / ((double)nsteps * c->p.kappa * dT * (double)c->p.nx * (double)c->p.ny), 0};
+  const int nb = (int)std::min<long long>(kBlocks, ((long long)N + kThreads - 1) / kThreads);
+  int li = 0;   // Lb[li] = lambda_{n+1} (zero before the last state)
+  bool have_next = false;
+  for (long long s = nck - 1; s >= 0; --s) {
+    const long long n0 = s * K;
+    const long long n1 = (s == nck - 1) ? nsteps : (s + 1) * K - 1;   // states n0..n1 of this segment
+    // restore the checkpoint into the recompute lattices and store the states as float64
+    unsigned char* src = ckp + (size_t)s * 2 * pbytes;
+    LB_CU(c, cudaMemcpyAsync(rbp, src, pbytes, cudaMemcpyDeviceToDevice, st));
+    LB_CU(c, cudaMemcpyAsync(rbp + pbytes, src + pbytes, pbytes, cudaMemcpyDeviceToDevice, st));
+    int rc = 0;
+    for (long long n = n0; n <= n1; ++n) {
+      KArgs a = make_args(c);
+      a.fin = rbp + (size_t)rc * 2 * pbytes;
+      a.gin = rbp + (size_t)rc * 2 * pbytes + pbytes;
+      double* Xn = Xs + (size_t)(n - n0) * 2 * Q * N;
+      LB_CU(c, c->ops->pops(a, Xn, Xn + Q * N, st));
+      if (n < n1) {
+        a.fout = rbp + (size_t)(1 - rc) * 2 * pbytes;
+        a.gout = rbp + (size_t)(1 - rc) * 2 * pbytes + pbytes;
+        LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, st));
+        rc ^= 1;
+      }
+    }
+    for (long long n = n1; n >= n0; --n) {
+      const double* Xn = Xs + (size_t)(n - n0) * 2 * Q * N;
+      par.include_nu = (n >= 1) ? 1 : 0;
+      macro_kernel<<<nb, kThreads, 0, st>>>(Xn, g, M);
+      force_fwd_kernel<<<nb, kThreads, 0, st>>>(g, par, M);
+      div_fwd_kernel<<<nb, kThreads, 0, st>>>(g, M);
+      double* Lcur = Lb[1 - li];
+      coll_adj_kernel<<<nb, kThreads, 0, st>>>(Xn, M, have_next ? Lb[li] : nullptr, g, par, Lcur, A, part);
+      vel_adj_kernel<<<nb, kThreads, 0, st>>>(M, g, par, A);
+      force_adj_kernel<<<nb, kThreads, 0, st>>>(M, g, par, A, Lcur, part);
+      LB_CU(c, cudaGetLastError());
+      li = 1 - li;
+      have_next = true;
+    }
+    if (s == 0 && dJ_dT0) {
+      init_grad_kernel<<<nb, kThreads, 0, st>>>(Lb[li], Xs, g, c->lam, static_cast<double*>(d0.p));
+      LB_CU(c, cudaGetLastError());
+    }
+  }
+  std::vector<double> hp((size_t)kBlocks * P_COUNT);
+  double hj[2];
+  LB_CU(c, cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  LB_CU(c, cudaMemcpyAsync(hj, jacc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (dJ_dT0) LB_CU(c, cudaMemcpyAsync(dJ_dT0, d0.p, N * sizeof(double), cudaMemcpyDeviceToHost, st));
+  LB_CU(c, cudaStreamSynchronize(st));
+  double s[P_COUNT] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < kBlocks; ++b)
+    for (int k = 0; k < P_COUNT; ++k) s[k] += hp[(size_t)b * P_COUNT + k];
+  if (J) *J = hj[0] / (double)nsteps;
+  if (dJ_dTd) *dJ_dTd = s[P_TD];
+  if (dJ_dTu) *dJ_dTu = s[P_TU];
+  if (dJ_dG) *dJ_dG = s[P_G];
+  return LB_OK;
+}

@@ -15,6 +15,7 @@
 
 #include "../../include/lb.h"
 #include "lb_launch.cuh"
+#include "lb_ctx.h"
 
 namespace tlbm {
 
@@ -85,42 +86,10 @@ __global__ void lb_validate_kernel(const double* __restrict__ rho, const double*
 
 using namespace tlbm;
 
-struct lb_ctx {
-  lb_params p;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  const PrecOps* ops = nullptr;
-  void* f[2] = {nullptr, nullptr};
-  void* g[2] = {nullptr, nullptr};
-  int cur = 0;
-  int N = 0, plane = 0;
-  int by = 8, zc = 0, tiles_x = 0, tiles_y = 0, ntiles = 0, nchunks = 0;
-  double lam = 0.0, rho0 = 0.0, T0 = 0.0;
-  double* part = nullptr;    // [nz][ntiles][NPART]
-  double* diag = nullptr;    // [nz + 8]
-  double* nu_acc = nullptr;  // [2]
-  double* fields = nullptr;  // [5][N] staging for host-bound lb_moments
-  double* pops = nullptr;    // [38][N] staging for host-bound lb_populations
-  long long step = 0;
-  std::string err;
-};
-
 namespace {
 
 const char* kNullCtxMsg = "null context";
 
-int fail(lb_ctx* c, int code, const std::string& what) {
-  if (c) c->err = what;
-  return code;
-}
-int cuda_fail(lb_ctx* c, const char* where, cudaError_t e) {
-  return fail(c, LB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
-}
-#define LB_CU(ctx, call)                                        \
-  do {                                                          \
-    cudaError_t e_ = (call);                                    \
-    if (e_ != cudaSuccess) return cuda_fail((ctx), #call, e_);  \
-  } while (0)
 
 const PrecOps* ops_for(int prec) {
   switch (prec) {
@@ -131,6 +100,8 @@ const PrecOps* ops_for(int prec) {
     default: return nullptr;
   }
 }
+
+}  // namespace
 
 KArgs make_args(const lb_ctx* c) {
   KArgs a;
@@ -154,6 +125,8 @@ KArgs make_args(const lb_ctx* c) {
 
 dim3 fused_grid(const lb_ctx* c) { return dim3(c->ntiles, c->nchunks); }
 
+namespace {
+
 void free_all(lb_ctx* c) {
   if (!c) return;
   for (int k = 0; k < 2; ++k) { cudaFree(c->f[k]); cudaFree(c->g[k]); }
@@ -161,18 +134,24 @@ void free_all(lb_ctx* c) {
   cudaFree(c->fields); cudaFree(c->pops);
 }
 
-// Moments pass into the plane partials, then Nu(z) and the global health values into diag.
-int run_diag(lb_ctx* c, bool accumulate) {
+}  // namespace
+
+// Moments pass into the plane partials, then Nu(z) and the global health values into diag;
+// Nu_mean is added to acc[0] (and 1 to acc[1]) when acc is not null.
+int run_diag_acc(lb_ctx* c, double* acc) {
   KArgs a = make_args(c);
   a.part = c->part;
   LB_CU(c, c->ops->fused(a, MODE_MOMENTS, c->by, fused_grid(c), c->stream));
   const int nz = c->p.nz;
   lb_diag_finalize<<<1, 256, 2 * nz * sizeof(double), c->stream>>>(
-      c->part, nz, c->ntiles, c->p.nx * c->p.ny, c->p.kappa, c->p.T_d, c->p.T_u, c->diag,
-      accumulate ? c->nu_acc : nullptr);
+      c->part, nz, c->ntiles, c->p.nx * c->p.ny, c->p.kappa, c->p.T_d, c->p.T_u, c->diag, acc);
   LB_CU(c, cudaGetLastError());
   return LB_OK;
 }
+
+int run_diag(lb_ctx* c, bool accumulate) { return run_diag_acc(c, accumulate ? c->nu_acc : nullptr); }
+
+namespace {
 
 uint64_t fnv1a(uint64_t h, const unsigned char* p, size_t n) {
   for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ull; }
@@ -324,7 +303,7 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
 
 int lb_step(lb_ctx* c, long long nsteps) {
   if (!c) return LB_EINVAL;
-  if (nsteps < 0) return fail(c, LB_EINVAL, "nsteps < 0");
+  if (nsteps < 0) return lb_fail(c, LB_EINVAL, "nsteps < 0");
   const dim3 grid = fused_grid(c);
   for (long long s = 0; s < nsteps; ++s) {
     KArgs a = make_args(c);
@@ -342,7 +321,7 @@ int lb_step(lb_ctx* c, long long nsteps) {
       LB_CU(c, cudaMemcpyAsync(h, c->diag + c->p.nz, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       LB_CU(c, cudaStreamSynchronize(c->stream));
       if (!(h[1] > 0.0) || !(h[2] > 0.0) || h[3] != 0.0)
-        return fail(c, LB_ENONPHYS, "health check failed at step " + std::to_string(c->step));
+        return lb_fail(c, LB_ENONPHYS, "health check failed at step " + std::to_string(c->step));
     }
   }
   return LB_OK;
@@ -355,7 +334,7 @@ int lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* uz, doubl
   const size_t N = (size_t)c->N;
   if (!on_device) {
     if (!c->fields && cudaMalloc(&c->fields, 5 * N * sizeof(double)) != cudaSuccess)
-      return fail(c, LB_ENOMEM, "moments staging");
+      return lb_fail(c, LB_ENOMEM, "moments staging");
     for (int k = 0; k < 5; ++k) if (outs[k]) outs[k] = c->fields + k * N;
   }
   a.rho_out = outs[0]; a.ux_out = outs[1]; a.uy_out = outs[2]; a.uz_out = outs[3]; a.T_out = outs[4];
@@ -372,7 +351,7 @@ int lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* uz, doubl
 }
 
 int lb_nusselt(lb_ctx* c, double* nu_mean, double* nu_z, double* nu_time_avg) {
-  if (!c || !nu_mean) return c ? fail(c, LB_EINVAL, "nu_mean is null") : LB_EINVAL;
+  if (!c || !nu_mean) return c ? lb_fail(c, LB_EINVAL, "nu_mean is null") : LB_EINVAL;
   int rc = run_diag(c, false);
   if (rc) return rc;
   const int nz = c->p.nz;
@@ -388,7 +367,7 @@ int lb_nusselt(lb_ctx* c, double* nu_mean, double* nu_z, double* nu_time_avg) {
 }
 
 int lb_diagnostics(lb_ctx* c, double out[5]) {
-  if (!c || !out) return c ? fail(c, LB_EINVAL, "out is null") : LB_EINVAL;
+  if (!c || !out) return c ? lb_fail(c, LB_EINVAL, "out is null") : LB_EINVAL;
   int rc = run_diag(c, false);
   if (rc) return rc;
   double h[5];
@@ -405,7 +384,7 @@ int lb_populations(lb_ctx* c, double* f, double* g, int on_device) {
   double* dg = g;
   if (!on_device) {
     if (!c->pops && cudaMalloc(&c->pops, 2 * n * sizeof(double)) != cudaSuccess)
-      return fail(c, LB_ENOMEM, "population staging");
+      return lb_fail(c, LB_ENOMEM, "population staging");
     df = f ? c->pops : nullptr;
     dg = g ? c->pops + n : nullptr;
   }
@@ -420,7 +399,7 @@ int lb_populations(lb_ctx* c, double* f, double* g, int on_device) {
 }
 
 int lb_save(lb_ctx* c, const char* path) {
-  if (!c || !path) return c ? fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
+  if (!c || !path) return c ? lb_fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
   const size_t pbytes = (size_t)Q * c->N * c->ops->esize;
   std::vector<unsigned char> buf(2 * pbytes);
   CkptHeader h;
@@ -435,27 +414,27 @@ int lb_save(lb_ctx* c, const char* path) {
   LB_CU(c, cudaStreamSynchronize(c->stream));
   h.checksum = fnv1a(1469598103934665603ull, buf.data(), buf.size());
   FILE* fp = std::fopen(path, "wb");
-  if (!fp) return fail(c, LB_EIO, std::string("cannot open ") + path);
+  if (!fp) return lb_fail(c, LB_EIO, std::string("cannot open ") + path);
   bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
   ok = (std::fclose(fp) == 0) && ok;
-  return ok ? LB_OK : fail(c, LB_EIO, std::string("write failed: ") + path);
+  return ok ? LB_OK : lb_fail(c, LB_EIO, std::string("write failed: ") + path);
 }
 
 int lb_load(lb_ctx* c, const char* path) {
-  if (!c || !path) return c ? fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
+  if (!c || !path) return c ? lb_fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
   FILE* fp = std::fopen(path, "rb");
-  if (!fp) return fail(c, LB_EIO, std::string("cannot open ") + path);
+  if (!fp) return lb_fail(c, LB_EIO, std::string("cannot open ") + path);
   CkptHeader h;
   const size_t pbytes = (size_t)Q * c->N * c->ops->esize;
   std::vector<unsigned char> buf(2 * pbytes);
   bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
   std::fclose(fp);
-  if (!ok) return fail(c, LB_EIO, "short read");
-  if (std::memcmp(h.magic, "TLBMCKP1", 8) != 0 || h.version != 1) return fail(c, LB_EIO, "bad magic/version");
+  if (!ok) return lb_fail(c, LB_EIO, "short read");
+  if (std::memcmp(h.magic, "TLBMCKP1", 8) != 0 || h.version != 1) return lb_fail(c, LB_EIO, "bad magic/version");
   if (h.nx != c->p.nx || h.ny != c->p.ny || h.nz != c->p.nz || h.precision != c->p.precision)
-    return fail(c, LB_EIO, "grid or precision mismatch");
+    return lb_fail(c, LB_EIO, "grid or precision mismatch");
   if (fnv1a(1469598103934665603ull, buf.data(), buf.size()) != h.checksum)
-    return fail(c, LB_EIO, "checksum mismatch");
+    return lb_fail(c, LB_EIO, "checksum mismatch");
   LB_CU(c, cudaMemcpyAsync(c->f[c->cur], buf.data(), pbytes, cudaMemcpyHostToDevice, c->stream));
   LB_CU(c, cudaMemcpyAsync(c->g[c->cur], buf.data() + pbytes, pbytes, cudaMemcpyHostToDevice, c->stream));
   LB_CU(c, cudaMemcpyAsync(c->nu_acc, h.nu_acc, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));

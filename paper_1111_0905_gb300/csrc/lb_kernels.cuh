@@ -294,6 +294,9 @@ lb_fused_kernel(const KArgs a) {
   else { hx = BX; hy = tid - 2 * BX - BY; }
 
   for (int p = z0 - 2; p <= z1 + 1; ++p) {
+    const int z = p - 2;            // plane collided by this iteration's C stage
+    const bool cplane = (z >= z0 && z < z1);
+    const bool wallz = (z == 0 || z == nz - 1);
     // ---------------- M: psi, rho, j of plane p on the radius-2 ring; f of the tile cached ----------------
     {
       const int pz = mirror_z(p, nz);
@@ -367,14 +370,11 @@ lb_fused_kernel(const KArgs a) {
     }
     __syncthreads();
     // ---------------- C: collide plane z = p-2 ----------------
-    const int z = p - 2;
-    const bool cplane = (z >= z0 && z < z1);
     // moments-mode partials of this thread's node (neutral values when it has none)
     double d_conv = 0.0, d_T = 0.0, d_rho = 0.0, d_E = 0.0, d_mr = 1e300, d_mT = 1e300, d_bad = 0.0;
     if (cplane && cvalid) {
       const unsigned own = (unsigned)z * plane + (unsigned)(crow[1] + ccol[1]);
       const int t = ty * BX + tx;
-      const bool wallz = (z == 0 || z == nz - 1);
       S gr[Q];
       if (wallz) pull_raw<S, true>(gr, gin, N, z, nz, plane, ccol, crow);
       else pull_raw<S, false>(gr, gin, N, z, nz, plane, ccol, crow);

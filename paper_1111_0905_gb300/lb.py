@@ -22,7 +22,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "libthermal_lbm.so"
 _lib = None
 
 # Names declared in include/lb.h.
-EXPORTS = ("lb_init", "lb_step", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
+EXPORTS = ("lb_init", "lb_step", "lb_adjoint_step", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
            "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error",
            "lb_nusselt_fields_noalloc")
 NOALLOC_MAX_NZ = 8192
@@ -114,6 +114,8 @@ def load_library():
     lib.lb_strerror.restype = ctypes.c_char_p
     lib.lb_last_error.argtypes = [P]
     lib.lb_last_error.restype = ctypes.c_char_p
+    lib.lb_adjoint_step.argtypes = [P, LL, I, DP, DP, DP, DP, P]
+    lib.lb_adjoint_step.restype = I
     lib.lb_nusselt_fields_noalloc.argtypes = [P, P, P, I, I, I, D, D, D, D, D, P, P]
     lib.lb_nusselt_fields_noalloc.restype = I
     _lib = lib
@@ -205,6 +207,16 @@ class Lattice:
     @property
     def step_count(self) -> int:
         return int(self.lib.lb_step_count(self.ctx))
+
+    def adjoint(self, nsteps: int, checkpoint_every: int = 50, grad_T0: bool = False) -> dict:
+        """lb_adjoint_step: J = time-averaged Nu over the next nsteps steps and dJ/d(T_d, T_u, G)
+        (and dJ/dT0 as [nz, ny, nx] if grad_T0; requires step 0)."""
+        J, dTd, dTu, dG = (ctypes.c_double() for _ in range(4))
+        dT0 = np.empty(self.shape, dtype=np.float64) if grad_T0 else None
+        self._check(self.lib.lb_adjoint_step(self.ctx, int(nsteps), int(checkpoint_every),
+                                             ctypes.byref(J), ctypes.byref(dTd), ctypes.byref(dTu),
+                                             ctypes.byref(dG), _ptr(dT0)), "lb_adjoint_step")
+        return {"J": J.value, "T_d": dTd.value, "T_u": dTu.value, "G": dG.value, "T0": dT0}
 
     def moments(self, device: bool = False):
         """(rho, (ux, uy, uz), T) as numpy [nz, ny, nx] arrays, or torch CUDA tensors if device."""

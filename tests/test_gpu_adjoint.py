@@ -1,0 +1,87 @@
+"""Discrete adjoint (lb_adjoint_step) against the oracle's exact gradient (PyTorch autograd
+through the plain FP64 steps) and against central finite differences on the GPU."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lbm
+from paper_1111_0905_gb300 import config, lb
+from helpers import oracle_params
+
+pytestmark = pytest.mark.gpu
+DT = torch.float64
+
+
+def _oracle_grad(p, rho, T, nsteps):
+    op = oracle_params(p)
+    Td = torch.tensor(p.T_d, dtype=DT, requires_grad=True)
+    Tu = torch.tensor(p.T_u, dtype=DT, requires_grad=True)
+    G = torch.tensor(p.G, dtype=DT, requires_grad=True)
+    T0 = torch.from_numpy(T).clone().requires_grad_(True)
+    q = lbm.Params(op.nx, op.ny, op.nz, op.tau_nu, op.tau_kappa, G, op.kappa, op.c_v, op.g_z, Td, Tu)
+    J = lbm.time_averaged_nusselt(torch.from_numpy(rho), T0, q, nsteps)
+    J.backward()
+    return {"J": J.item(), "T_d": Td.grad.item(), "T_u": Tu.grad.item(), "G": G.grad.item(),
+            "T0": T0.grad.numpy()}
+
+
+@pytest.mark.parametrize("shape,nsteps,K", [((8, 6, 7), 12, 5), ((5, 4, 3), 9, 9), ((33, 3, 4), 6, 2)])
+def test_adjoint_matches_oracle_gradient(lblib, cuda, shape, nsteps, K):
+    nx, ny, nz = shape
+    w = config.boiling_cell(nx, nz=nz, ny=ny)
+    rho, T = w.fields()
+    lat = lb.Lattice(w.params, rho, T)
+    got = lat.adjoint(nsteps, K, grad_T0=True)
+    lat.close()
+    ref = _oracle_grad(w.params, rho, T, nsteps)
+    assert abs(got["J"] - ref["J"]) <= 1e-11 * max(1.0, abs(ref["J"]))
+    for k in ("T_d", "T_u", "G"):
+        assert abs(got[k] - ref[k]) <= 1e-9 * max(1.0, abs(ref[k])), (k, got[k], ref[k])
+    scale = np.abs(ref["T0"]).max()
+    assert np.abs(got["T0"] - ref["T0"]).max() <= 1e-9 * scale
+
+
+def _J_gpu(p, rho, T, nsteps):
+    q = lb.Params(**{**p.__dict__, "nu_every": 1})
+    lat = lb.Lattice(q, rho, T)
+    lat.step(nsteps)
+    J = lat.nusselt()[2]
+    lat.close()
+    return J
+
+
+def test_adjoint_matches_central_differences_boiling_32(lblib, cuda):
+    """The 32^3 boiling cell over 200 steps (checkpoints every 50): dJ/d(T_d, T_u, G) and a
+    random direction of dJ/dT0 against central differences (h = 1e-6) within 1e-4."""
+    w = config.boiling_cell(32)
+    p = w.params
+    rho, T = w.fields()
+    N, K = 200, 50
+    lat = lb.Lattice(p, rho, T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got = lat.adjoint(N, K, grad_T0=True)
+    t_adj = time.perf_counter() - t0
+    lat.close()
+    lat = lb.Lattice(p, rho, T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.step(N)
+    lat.nusselt()
+    t_fwd = time.perf_counter() - t0
+    lat.close()
+    print(f"adjoint {t_adj:.3f} s vs forward {t_fwd:.3f} s ({t_adj / t_fwd:.2f}x)")
+    assert abs(got["J"] - _J_gpu(p, rho, T, N)) <= 1e-12 * abs(got["J"])
+    h = 1e-6
+    for k in ("T_d", "T_u", "G"):
+        base = getattr(p, k)
+        Jp = _J_gpu(lb.Params(**{**p.__dict__, k: base + h}), rho, T, N)
+        Jm = _J_gpu(lb.Params(**{**p.__dict__, k: base - h}), rho, T, N)
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(fd - got[k]) <= 1e-4 * max(abs(fd), 1e-3), (k, fd, got[k])
+    v = np.random.default_rng(5).standard_normal(T.shape)
+    fd = (_J_gpu(p, rho, T + h * v, N) - _J_gpu(p, rho, T - h * v, N)) / (2 * h)
+    ad = float((got["T0"] * v).sum())
+    assert abs(fd - ad) <= 1e-4 * max(abs(fd), 1e-3), (fd, ad)
