@@ -187,7 +187,8 @@ def run_ours(args):
     fields = {}
     main_form = "f32"
     clock_summary = None
-    for form in ["f32", "f64", "bf16dev", "fp16dev"]:
+    form_list = [args.only] if args.only else ["f32", "f64", "bf16dev", "fp16dev"]
+    for form in form_list:
         w = workload(form)
         p = w.params
         N = p.nx * p.ny * p.nz
@@ -225,6 +226,12 @@ def run_ours(args):
         del rho_d, T_d
         torch.cuda.empty_cache()
 
+    if args.only:
+        if rank == 0:
+            print(json.dumps({"only": args.only, "form": results[args.only]}))
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
     r64, u64, T64, nu64 = fields["f64"]
     for form, (r, u, TT, nu) in fields.items():
         results[form]["err_vs_f64"] = None if form == "f64" else {
@@ -260,6 +267,9 @@ def run_ours(args):
            "what": "lb_init from pinned host rho,T + lb_step(K) + lb_nusselt + lb_moments to "
                    "pinned host, wall clock"}
 
+    # the sizes the HBM target is stated at (256^3, 512^3), same kernel, paper-geometry boiling cell
+    sizes = {} if args.no_sizes else size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws)
+
     main = results[main_form]
     src_hash = kernel_src_hash()
     traffic = None
@@ -281,10 +291,43 @@ def run_ours(args):
                "data": "synthetic (seeded SplitMix64 fields; no dataset)",
                "config": config_dict(w, main_form), "roofline": roofline, "cpu_baseline": cpu,
                "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_summary,
-               "forms": results, "kernel_src_hash": src_hash}
+               "forms": results, "sizes": sizes, "kernel_src_hash": src_hash}
         print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
+    return out
+
+
+def size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
+    """GLUPS and HBM fraction of the FP32 and FP16-deviation forms on the boiling cell at 256^3
+    and 512^3 (50 timed steps after 10 warm-up steps each)."""
+    from paper_1111_0905_gb300 import config
+    out = {}
+    for n in (256, 512):
+        for form in ("f32", "fp16dev"):
+            w = config.paper_scale_cell(n, precision=FORMS[form])
+            p = w.params
+            N = p.nx * p.ny * p.nz
+            rho, T = w.fields()
+            lat = lb.Lattice(p, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+            del rho, T
+            lat.step(10)
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            K = 50
+            e0.record()
+            lat.step(K)
+            e1.record()
+            e1.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1)) / K
+            lat.close()
+            torch.cuda.empty_cache()
+            bytes_step = 4 * Q * STORE_BYTES[form] * N
+            out[f"{n}^3_{form}"] = {"glups": N / (ms * 1e-3) / 1e9 * ws, "ms_per_step": ms,
+                                    "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                    "workload": w.name}
     return out
 
 
@@ -365,6 +408,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sizes", action="store_true", help="skip the 256^3/512^3 measurements")
+    ap.add_argument("--only", choices=list(FORMS), help="time one form of the 128^3 cell only "
+                    "(no errors, e2e or baselines; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

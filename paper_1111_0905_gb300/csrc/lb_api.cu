@@ -114,6 +114,11 @@ KArgs make_args(const lb_ctx* c) {
   a.G = c->p.G; a.g_z = c->p.g_z; a.lam = c->lam; a.inv_cv = 1.0 / c->p.c_v; a.c_v = c->p.c_v;
   a.kappa = c->p.kappa; a.T_d = c->p.T_d; a.T_u = c->p.T_u;
   a.rho0 = c->rho0; a.T0 = c->T0; a.E0 = c->rho0 * c->T0;
+  a.pd = {a.tau_nu, a.omega_nu, a.omega_kappa, a.G, a.g_z, a.lam, a.inv_cv, a.T_d, a.T_u,
+          a.rho0, a.T0, a.E0};
+  a.pf = {(float)a.tau_nu, (float)a.omega_nu, (float)a.omega_kappa, (float)a.G, (float)a.g_z,
+          (float)a.lam, (float)a.inv_cv, (float)a.T_d, (float)a.T_u, (float)a.rho0, (float)a.T0,
+          (float)a.E0};
   // reference equilibria per class (rest, axis, diagonal): f^eq(rho0, 0, T0), g^eq(rho0, T0, 0)
   const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
   for (int k = 0; k < 3; ++k) {

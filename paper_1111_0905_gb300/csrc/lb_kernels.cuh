@@ -83,6 +83,12 @@ template <> struct Store<__half> {
 };
 
 
+// Parameters of the hot path in the compute precision R, precomputed on the host so that the
+// FP32 kernels never convert from double (conversions run on GB300's narrow FP64 pipe).
+template <class R> struct KPar {
+  R tau_nu, omega_nu, omega_kappa, G, g_z, lam, inv_cv, T_d, T_u, rho0, T0, E0;
+};
+
 struct KArgs {
   const void* fin; const void* gin;   // post-collision lattices of the previous step
   void* fout; void* gout;             // lattices written by this step
@@ -94,7 +100,13 @@ struct KArgs {
   // moments mode outputs (any may be null)
   double* rho_out; double* ux_out; double* uy_out; double* uz_out; double* T_out;
   double* part;                       // [nz][ntiles][NPART] diagnostics partials (may be null)
+  KPar<double> pd;                    // the parameters above in double ...
+  KPar<float> pf;                     // ... and in float
 };
+
+template <class R> __device__ __forceinline__ const KPar<R>& kpar(const KArgs& a);
+template <> __device__ __forceinline__ const KPar<double>& kpar<double>(const KArgs& a) { return a.pd; }
+template <> __device__ __forceinline__ const KPar<float>& kpar<float>(const KArgs& a) { return a.pf; }
 
 __host__ __device__ __forceinline__ int wrapi(int a, int n) { int m = a % n; return m < 0 ? m + n : m; }
 // Plane index of the reflection of plane k across the halfway walls (applied repeatedly).
@@ -258,8 +270,9 @@ lb_fused_kernel(const KArgs a) {
   const int z0 = blockIdx.y * a.zc;
   const int z1 = min(z0 + a.zc, nz);
 
-  const R rho0 = R(a.rho0), E0 = R(a.E0), T0 = R(a.T0);
-  const R G = R(a.G), gz = R(a.g_z), lam = R(a.lam), Td = R(a.T_d), Tu = R(a.T_u);
+  const KPar<R>& kp = kpar<R>(a);
+  const R rho0 = kp.rho0, E0 = kp.E0, T0 = kp.T0;
+  const R G = kp.G, gz = kp.g_z, lam = kp.lam, Td = kp.T_d, Tu = kp.T_u;
 
   // Ring nodes of the M stage owned by this thread: wrapped columns/rows of x-1, x, x+1.
   int mcol[MAXM][3], mrow[MAXM][3];
@@ -414,7 +427,7 @@ lb_fused_kernel(const KArgs a) {
         // w [drho - 1.5 rho v.v + 4.5 (|c|^2-1)(dE - drho/3) + 3 rho c.v + 4.5 rho (c.v)^2]
         // (rho (T - 1/3) - rho0 (T0 - 1/3) = dE - drho/3 since rho T = E).
         {
-          const R tau = R(a.tau_nu), om = R(a.omega_nu), om1 = R(1) - om;
+          const R tau = kp.tau_nu, om = kp.omega_nu, om1 = R(1) - om;
           const R vx = (jx + tau * Fx) * inv, vy = (jy + tau * Fy) * inv, vz = (jz + tau * Fz) * inv;
           const R a0 = drho - R(1.5) * rho * (vx * vx + vy * vy + vz * vz);
           const R th = R(4.5) * (dE - drho * R(1.0 / 3.0));
@@ -435,8 +448,8 @@ lb_fused_kernel(const KArgs a) {
         // g^eq - gbase per class: w [dE - 1.5 E u.u + 4.5 (|c|^2-1)(lam (T-T0) - dE/3) + 3 E c.u
         // + 4.5 E (c.u)^2], T - T0 = (dE - T0 drho)/rho.
         {
-          const R omk = R(a.omega_kappa), omk1 = R(1) - omk;
-          const R Ssrc = -E * D * R(a.inv_cv);
+          const R omk = kp.omega_kappa, omk1 = R(1) - omk;
+          const R Ssrc = -E * D * kp.inv_cv;
           const R b0 = dE - R(1.5) * E * (ux * ux + uy * uy + uz * uz);
           const R tg = R(4.5) * (lam * ((dE - T0 * drho) * inv) - dE * R(1.0 / 3.0));
           const R B[3] = {b0 - tg, b0, b0 + tg};
