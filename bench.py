@@ -280,7 +280,7 @@ def run_ours(args):
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": bytes_launch / (main["ms_per_step"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
                 "traffic": traffic, "peak_src": peaks["src"] + " (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": "tlbm::lb_fused_kernel<float,16,0>", "algorithmic_bytes_per_launch": bytes_launch}
+                "kernel": "tlbm::lb_fused_kernel<float,8,0>", "algorithmic_bytes_per_launch": bytes_launch}
 
     out = None
     if rank == 0:

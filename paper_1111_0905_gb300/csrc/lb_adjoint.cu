@@ -346,7 +346,7 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
 
   DevBuf ck, rb, xs, mb, ab, lb, pt, acc, d0;
   if (cudaMalloc(&ck.p, (size_t)nck * 2 * pbytes) != cudaSuccess ||
-      cudaMalloc(&rb.p, 4 * pbytes) != cudaSuccess ||
+      cudaMalloc(&rb.p, 4 * pbytes + 64) != cudaSuccess ||
       cudaMalloc(&xs.p, (size_t)(K + 1) * sbytes) != cudaSuccess ||
       cudaMalloc(&mb.p, (size_t)MF_COUNT * N * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&ab.p, (size_t)AF_COUNT * N * sizeof(double)) != cudaSuccess ||

@@ -208,8 +208,8 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   if (!std::isfinite(p.G) || !std::isfinite(p.g_z) || !(p.T_d > 0.0) || !(p.T_u > 0.0)) return LB_EINVAL;
   const PrecOps* ops = ops_for(p.precision);
   if (!ops) return LB_EINVAL;
-  // default tile height: 32 x 16 for FP32, 32 x 8 otherwise (measured best on the 128^3/256^3 cells)
-  int by = p.tile_y != 0 ? p.tile_y : (p.precision == LB_FP32 ? 16 : 8);
+  // default tile height 32 x 8 (measured best on the 128^3/256^3 cells for every form)
+  int by = p.tile_y != 0 ? p.tile_y : 8;
   if (by != 4 && by != 8 && by != 16) return LB_EINVAL;
   if (!ops->tile_ok(by)) return LB_EINVAL;
   if ((long long)Q * N >= (1ll << 32)) return LB_EINVAL;   // 32-bit population offsets
@@ -273,7 +273,8 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   c->rho0 = p.rho0 > 0 ? p.rho0 : sr / N;
   c->T0 = p.T0 > 0 ? p.T0 : sT / N;
 
-  const size_t pbytes = (size_t)Q * N * ops->esize;
+  // 64 bytes of padding: the staged 16-bit pulls copy the 4-byte word containing an element
+  const size_t pbytes = (size_t)Q * N * ops->esize + 64;
   for (int k = 0; k < 2; ++k) {
     if (cudaMalloc(&c->f[k], pbytes) != cudaSuccess || cudaMalloc(&c->g[k], pbytes) != cudaSuccess) {
       cudaFree(staging);

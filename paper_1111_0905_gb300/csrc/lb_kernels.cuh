@@ -22,6 +22,10 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#ifndef TLBM_STAGE
+#define TLBM_STAGE 1
+#endif
+
 namespace tlbm {
 
 constexpr int Q = 19;
@@ -192,12 +196,14 @@ template <int BY> struct Geo {
   static constexpr int MAXM = (RXY + NT - 1) / NT;
   static constexpr int NHALO = 2 * BX + 2 * BY;
   // R units: psi[3][RXY], rj[3][5][HXY] (rho, 1/rho, jx, jy, jz), u[3][3][HXY], F[2][3][TXY];
-  // then the pulled-f cache of the tile, fc[3][Q][TXY] in storage units S.
+  // then either the pulled-f cache of the tile, fc[3][Q][TXY] in storage units S, or (STG) the
+  // stage of the collision's pulled f and g, stg[2][Q][TXY] in 4-byte words.
   template <class R> static constexpr size_t r_count() {
     return (size_t)(3 * RXY + 15 * HXY + 9 * HXY + 6 * TXY);
   }
-  template <class S, class R> static constexpr size_t smem_bytes() {
-    return sizeof(R) * r_count<R>() + sizeof(S) * (size_t)(3 * Q * TXY);
+  template <class S, class R, bool STG> static constexpr size_t smem_bytes() {
+    return sizeof(R) * r_count<R>() +
+           (STG ? sizeof(uint32_t) * (size_t)(2 * Q * TXY) : sizeof(S) * (size_t)(3 * Q * TXY));
   }
 };
 
@@ -233,6 +239,39 @@ __device__ __forceinline__ void pull_raw(S (&v)[Q], const S* __restrict__ buf, u
   }
 }
 
+// Element index of the pulled source of population l at node (col[1], row[1], z) (through a wall,
+// when WALL, the bounce-back source opp(l) of the node itself).
+template <bool WALL>
+__device__ __forceinline__ unsigned pull_index(int l, unsigned N, int z, int nz, unsigned plane,
+                                               const int (&col)[3], const int (&row)[3]) {
+  const int cz = CZ(l);
+  if (WALL && ((cz > 0 && z == 0) || (cz < 0 && z == nz - 1)))
+    return (unsigned)OPP(l) * N + (unsigned)z * plane + (unsigned)(row[1] + col[1]);
+  return (unsigned)l * N + ((unsigned)z * plane - (unsigned)(cz * (int)plane)) +
+         (unsigned)(row[1 - CY(l)] + col[1 - CX(l)]);
+}
+
+// 4-byte asynchronous global -> shared copy (cp.async, cached in L1 and L2); a 16-bit element is
+// copied as the aligned 4-byte word that contains it (population arrays carry 64 bytes of padding).
+template <class S>
+__device__ __forceinline__ void stage_word(uint32_t* dst, const S* base, unsigned e) {
+  const S* src = base + (sizeof(S) == 2 ? (e & ~1u) : e);
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <class S> __device__ __forceinline__ S word_elem(uint32_t w, unsigned e);
+template <> __device__ __forceinline__ float word_elem<float>(uint32_t w, unsigned) { return __uint_as_float(w); }
+template <> __device__ __forceinline__ __half word_elem<__half>(uint32_t w, unsigned e) {
+  return __ushort_as_half((unsigned short)((e & 1u) ? (w >> 16) : (w & 0xffffu)));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 word_elem<__nv_bfloat16>(uint32_t w, unsigned e) {
+  return __ushort_as_bfloat16((unsigned short)((e & 1u) ? (w >> 16) : (w & 0xffffu)));
+}
+template <> __device__ __forceinline__ double word_elem<double>(uint32_t, unsigned) { return 0.0; }
+
 template <class S, class R>
 __device__ __forceinline__ R cvt(S v) { return Store<S>::ld(&v); }
 template <> __device__ __forceinline__ double cvt<double, double>(double v) { return v; }
@@ -254,11 +293,15 @@ lb_fused_kernel(const KArgs a) {
   constexpr int TXY = GE::TXY, MAXM = GE::MAXM, NHALO = GE::NHALO;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool STG = std::is_same<S, float>::value && TLBM_STAGE;
   R* psi_s = reinterpret_cast<R*>(smem_raw);  // [3][RXY]
   R* rj_s = psi_s + 3 * RXY;                  // [3][5][HXY]  rho, 1/rho, jx, jy, jz
   R* u_s = rj_s + 15 * HXY;                   // [3][3][HXY]  physical velocity
   R* F_s = u_s + 9 * HXY;                     // [2][3][TXY]  force on the tile
-  S* fc_s = reinterpret_cast<S*>(F_s + 6 * TXY);  // [3][Q][TXY] pulled f of the tile
+  // FP32 stages the collision's pulled f and g asynchronously; FP64 and the 16-bit forms keep
+  // the f cache (measured faster for them) and pull g directly.
+  S* fc_s = reinterpret_cast<S*>(F_s + 6 * TXY);                 // [3][Q][TXY] (not STG)
+  uint32_t* stg_s = reinterpret_cast<uint32_t*>(F_s + 6 * TXY);  // [2][Q][TXY] (STG)
 
   const S* __restrict__ fin = static_cast<const S*>(a.fin);
   const S* __restrict__ gin = static_cast<const S*>(a.gin);
@@ -310,6 +353,20 @@ lb_fused_kernel(const KArgs a) {
     const int z = p - 2;            // plane collided by this iteration's C stage
     const bool cplane = (z >= z0 && z < z1);
     const bool wallz = (z == 0 || z == nz - 1);
+    if constexpr (STG) {
+      // start the copies of the collision's pulled f and g; they complete behind M and U
+      if (cplane && cvalid) {
+        const int t = ty * BX + tx;
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const unsigned e = wallz ? pull_index<true>(l, N, z, nz, plane, ccol, crow)
+                                   : pull_index<false>(l, N, z, nz, plane, ccol, crow);
+          stage_word<S>(stg_s + l * TXY + t, fin, e);
+          stage_word<S>(stg_s + (Q + l) * TXY + t, gin, e);
+        }
+      }
+      stage_commit();
+    }
     // ---------------- M: psi, rho, j of plane p on the radius-2 ring; f of the tile cached ----------------
     {
       const int pz = mirror_z(p, nz);
@@ -335,7 +392,7 @@ lb_fused_kernel(const KArgs a) {
             R* rj = rj_s + s3 * 5 * HXY + mh[i];
             rj[0] = rho; rj[HXY] = inv; rj[2 * HXY] = jx; rj[3 * HXY] = jy; rj[4 * HXY] = jz;
           }
-          if (real && mt[i] >= 0) {
+          if (!STG && real && mt[i] >= 0) {
             S* fc = fc_s + s3 * Q * TXY + mt[i];
 #pragma unroll
             for (int l = 0; l < Q; ++l) fc[l * TXY] = fr[l];
@@ -388,17 +445,27 @@ lb_fused_kernel(const KArgs a) {
     if (cplane && cvalid) {
       const unsigned own = (unsigned)z * plane + (unsigned)(crow[1] + ccol[1]);
       const int t = ty * BX + tx;
-      S gr[Q];
-      if (wallz) pull_raw<S, true>(gr, gin, N, z, nz, plane, ccol, crow);
-      else pull_raw<S, false>(gr, gin, N, z, nz, plane, ccol, crow);
-      R g[Q];
+      R g[Q], f[Q];
+      if constexpr (STG) {
+        stage_wait();                  // this thread's copies of the collision's f and g
 #pragma unroll
-      for (int l = 0; l < Q; ++l) g[l] = cvt<S, R>(gr[l]);
+        for (int l = 0; l < Q; ++l) {
+          const unsigned e = wallz ? pull_index<true>(l, N, z, nz, plane, ccol, crow)
+                                   : pull_index<false>(l, N, z, nz, plane, ccol, crow);
+          f[l] = cvt<S, R>(word_elem<S>(stg_s[l * TXY + t], e));
+          g[l] = cvt<S, R>(word_elem<S>(stg_s[(Q + l) * TXY + t], e));
+        }
+      } else {
+        S gr[Q];
+        if (wallz) pull_raw<S, true>(gr, gin, N, z, nz, plane, ccol, crow);
+        else pull_raw<S, false>(gr, gin, N, z, nz, plane, ccol, crow);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) g[l] = cvt<S, R>(gr[l]);
+        const S* fc = fc_s + slot3(z) * Q * TXY + t;
+#pragma unroll
+        for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fc[l * TXY]);
+      }
       if (wallz) g_wall_fix<S, R>(g, fin, (int)N, (int)own, z, nz, rho0, T0, Td, Tu, lam);
-      const S* fc = fc_s + slot3(z) * Q * TXY + t;
-      R f[Q];
-#pragma unroll
-      for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fc[l * TXY]);
       const int cc = (ty + 1) * HX + (tx + 1);
       const R* rjc = rj_s + slot3(z) * 5 * HXY + cc;
       const R rho = rjc[0], inv = rjc[HXY];

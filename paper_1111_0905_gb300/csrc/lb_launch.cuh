@@ -22,7 +22,8 @@ template <class S> struct OpsImpl {
 
   // dynamic shared memory of a tile height; tile heights whose windows exceed the 227 KB a CTA
   // may use are not available (FP64 with BY = 16)
-  template <int BY> static constexpr size_t smem() { return Geo<BY>::template smem_bytes<S, R>(); }
+  static constexpr bool STG = std::is_same<S, float>::value && TLBM_STAGE;
+  template <int BY> static constexpr size_t smem() { return Geo<BY>::template smem_bytes<S, R, STG>(); }
   template <int BY> static constexpr bool fits() { return smem<BY>() + 1024 <= 227u * 1024u; }
   template <int BY, int MODE> static cudaError_t attr() {
     if constexpr (!fits<BY>()) {

@@ -1,0 +1,122 @@
+"""Physics validation of the CUDA path at GPU scale (the paper's Fig. 1 checks and the
+classical limits), each with its oracle counterpart at small size in the CPU tests.
+
+- Flat liquid slabs at T/T_c = 0.80 ... 0.95: bulk densities vs the Maxwell construction of
+  P = rho T + (G/2) e^{-2/rho}, and the Clausius-Clapeyron relation dP/dT = Delta s / Delta v
+  along the simulated coexistence curve (Fig. 1).
+- Static 3-D bubbles: Laplace law Delta P = 2 sigma / R (linear in 1/R).
+- Conduction below onset: linear T between the walls and Nu = 1.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import eos
+from paper_1111_0905_gb300 import config, lb
+
+pytestmark = pytest.mark.gpu
+G0 = config.G_DEFAULT
+TC = config.T_C
+
+
+def _run(p, rho, T, steps, precision=lb.LB_FP64):
+    q = lb.Params(**{**p.__dict__, "precision": precision})
+    lat = lb.Lattice(q, rho, T)
+    lat.step(steps)
+    r, u, TT = lat.moments()
+    lat.close()
+    return r, u, TT
+
+
+def _slab(t, nz=96, steps=30000):
+    T0 = t * TC
+    rg, rl = eos.coexistence(T0, G0)
+    p = lb.Params(nx=4, ny=4, nz=nz, tau_nu=1.0, tau_kappa=1.0, G=G0, kappa=0.24, g_z=0.0,
+                  T_d=T0, T_u=T0)
+    z = np.arange(nz) + 0.5
+    prof = 0.5 * (np.tanh((z - nz / 4) / 2.5) - np.tanh((z - 3 * nz / 4) / 2.5))
+    rho = np.broadcast_to((rg + (rl - rg) * prof)[:, None, None], (nz, 4, 4)).copy()
+    T = np.full_like(rho, T0)
+    r, u, TT = _run(p, rho, T, steps)
+    return r[nz // 2].mean(), r[1].mean(), rl, rg, float(np.abs(TT / T0 - 1).max())
+
+
+def test_flat_interfaces_maxwell_and_clausius_clapeyron():
+    ts = [0.80, 0.85, 0.90, 0.95]
+    res = {t: _slab(t) for t in ts}
+    for t, (rl_m, rg_m, rl, rg, dT) in res.items():
+        print(f"T/Tc={t}: rho_l {rl_m:.5f} (Maxwell {rl:.5f}, {100*(rl_m/rl-1):+.2f} %), "
+              f"rho_g {rg_m:.5f} (Maxwell {rg:.5f}, {100*(rg_m/rg-1):+.2f} %), max |dT/T| {dT:.1e}")
+        assert abs(rl_m / rl - 1) < 0.02 and abs(rg_m / rg - 1) < 0.06 and dT < 1e-2
+    # Clausius-Clapeyron on the simulated coexistence curve: P_sat(T) from the bulk EOS at the
+    # measured liquid density; dP/dT by central differences vs Delta s / Delta v at the centre
+    for i in (1, 2):
+        tm, t0, tp = ts[i - 1], ts[i], ts[i + 1]
+        P = lambda t: eos.pressure(res[t][0], t * TC, G0)
+        dPdT = (P(tp) - P(tm)) / ((tp - tm) * TC)
+        rl_m, rg_m = res[t0][0], res[t0][1]
+        ds_dv = math.log(rl_m / rg_m) / (1 / rg_m - 1 / rl_m)
+        print(f"T/Tc={t0}: dP/dT {dPdT:.5f} vs Delta s/Delta v {ds_dv:.5f} ({100*(dPdT/ds_dv-1):+.2f} %)")
+        # at tau_nu = 1 the velocity-shift forcing biases the coexistence densities (largest in
+        # the vapour at low T), which the relation inherits; the paper's tau_nu = 0.55 would
+        # reduce the bias ~100x but is linearly unstable under these readings
+        assert abs(dPdT / ds_dv - 1) < 0.10
+
+
+def test_laplace_law_for_static_droplets():
+    """Liquid droplets of radius R in vapour at T = 0.9 T_c, far from the walls: the pressure
+    jump from the bulk EOS is linear in 1/R with an intercept near zero. The droplets start from
+    the lattice's own flat-interface densities at this T (measured above: 0.5815, 1.8047)."""
+    T0 = 0.9 * TC
+    rg, rl = 0.5815, 1.8047
+    n = 80
+    p = lb.Params(nx=n, ny=n, nz=n, tau_nu=1.0, tau_kappa=1.0, G=G0, kappa=0.24, g_z=0.0,
+                  T_d=T0, T_u=T0)
+    c = (np.arange(n) + 0.5 - n / 2)
+    r3 = np.sqrt(c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2)
+    inv_R, dP = [], []
+    for R in (10.0, 14.0, 18.0):
+        rho = rg + (rl - rg) * 0.5 * (1 - np.tanh((r3 - R) / 2.5))
+        T = np.full_like(rho, T0)
+        r, u, TT = _run(p, rho, T, 12000, precision=lb.LB_FP32)
+        P = eos.pressure(r, TT, G0)
+        P_in = P[n // 2 - 1:n // 2 + 1, n // 2 - 1:n // 2 + 1, n // 2 - 1:n // 2 + 1].mean()
+        P_out = P[n // 2, n // 2, 2:6].mean()
+        # equimolar radius from the excess mass over the vapour, with the measured bulk densities
+        rho_in = r[n // 2 - 1:n // 2 + 1, n // 2 - 1:n // 2 + 1, n // 2 - 1:n // 2 + 1].mean()
+        rho_out = r[n // 2, n // 2, 2:6].mean()
+        vol = float(np.sum(r - rho_out) / (rho_in - rho_out))
+        R_eq = (3.0 * vol / (4.0 * math.pi)) ** (1.0 / 3.0)
+        assert R_eq > 4, f"droplet of initial radius {R} did not survive (R = {R_eq})"
+        inv_R.append(1.0 / R_eq)
+        dP.append(P_in - P_out)
+        print(f"R0={R}: R={R_eq:.2f}, dP={P_in - P_out:.5e}, max|u|={np.abs(np.stack(u)).max():.2e}")
+    A = np.vstack([inv_R, np.ones(3)]).T
+    (slope, icpt), res, *_ = np.linalg.lstsq(A, np.array(dP), rcond=None)
+    pred = A @ np.array([slope, icpt])
+    r2 = 1 - np.sum((np.array(dP) - pred) ** 2) / np.sum((np.array(dP) - np.mean(dP)) ** 2)
+    print(f"Laplace: 2 sigma = {slope:.5e}, intercept {icpt:.2e}, R^2 = {r2:.5f}")
+    assert slope > 0 and r2 > 0.995 and abs(icpt) < 0.1 * abs(slope) * max(inv_R)
+
+
+def test_conduction_profile_and_nusselt_one():
+    """No gravity, single phase: steady T linear between T_d (z=-1/2) and T_u (z=nz-1/2),
+    fluid at rest, Nu(z) = 1."""
+    nz = 32
+    Td, Tu = config.T_D, config.T_U
+    p = lb.Params(nx=16, ny=16, nz=nz, tau_nu=1.0, tau_kappa=1.0, G=0.0, kappa=0.3, g_z=0.0,
+                  T_d=Td, T_u=Tu)
+    z = (np.arange(nz) + 0.5) / nz
+    Tlin = Td + (Tu - Td) * z
+    T = np.broadcast_to(Tlin[:, None, None], (nz, 16, 16)).copy()
+    rho = (1.0 / 3.0) / T
+    lat = lb.Lattice(p, rho, T)
+    lat.step(20000)
+    r, u, TT = lat.moments()
+    nu_mean, nu_z, _ = lat.nusselt()
+    lat.close()
+    assert np.abs(TT[:, 0, 0] - Tlin).max() < 1e-8
+    assert np.abs(np.stack(u)).max() < 1e-8
+    assert np.abs(nu_z - 1).max() < 1e-6
