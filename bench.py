@@ -40,7 +40,8 @@ ERR_STEPS = 200
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the fused step
 # kernel from an ncu capture, keyed by the hash of the kernel sources it was taken on; it is
 # reported as null when the sources have changed since.
-TRAFFIC = {"src_hash": None, "bytes_per_launch": {}}
+TRAFFIC = {"src_hash": "0834d8f325af8226",
+           "bytes_per_launch": {"f32": 337872384 + 275959552, "fp16dev": 166958592 + 118238208}}
 
 
 def kernel_src_hash() -> str:
