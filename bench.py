@@ -114,6 +114,19 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def replica_aggregate(local_ms: float, nodes_per_rank: int, steps: int, ws: int, device="cpu"):
+    """Whole-job result of N independent replicas: the max over ranks of the timed milliseconds
+    and the whole-job GLUPS = all ranks' node updates / that max time (weak scaling)."""
+    import torch
+    ms = local_ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, nodes_per_rank * steps * ws / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -158,11 +171,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_aggregate(x, 1, 1, ws, device="cuda")[0]
 
     def time_steps(lat, K, W, clocks=None):
         lat.step(W)
