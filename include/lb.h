@@ -132,6 +132,29 @@ int lb_populations(lb_ctx* ctx, double* f, double* g, int on_device);
  * sum rho, out[4] = total sum rho T. FP64 reductions. Errors: LB_EINVAL, LB_ECUDA. */
 int lb_diagnostics(lb_ctx* ctx, double out[5]);
 
+/* lb_profiles -- per-plane means of the current state (the T(z) profile and its asymmetry, Fig. 2
+ * top inset, and the P div(u) term of the integral constraint of Eq. (5)): rho_z[z] = <rho>_{x,y},
+ * T_z[z] = <T>_{x,y}, PdivU_z[z] = <P div(u)>_{x,y} with P = rho T + (G/2) e^{-2/rho} and the
+ * divergence of the physical velocity by central differences (u_z -> -u_z across the walls).
+ * Host outputs of nz values; any may be NULL. FP64 sums in a fixed order. Synchronises.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+int lb_profiles(lb_ctx* ctx, double* rho_z, double* T_z, double* PdivU_z);
+
+/* lb_histogram_T_rho -- joint histogram of (T, rho) of the nodes in planes [z_lo, z_hi) (the T-rho
+ * scatter of Fig. 2 top, per region): counts[iT * nrho + irho] (host, uint64, nT * nrho <= 12288),
+ * bin = floor((v - lo) / (hi - lo) * n) for lo <= v < hi; values outside are not counted.
+ * Synchronises. Errors: LB_EINVAL (ranges), LB_ENOMEM, LB_ECUDA. */
+int lb_histogram_T_rho(lb_ctx* ctx, int z_lo, int z_hi, int nT, double T_lo, double T_hi, int nrho,
+                       double rho_lo, double rho_hi, unsigned long long* counts);
+
+/* lb_structure_functions -- horizontal structure functions of the vertical velocity and of the
+ * temperature over the planes [z_lo, z_hi) (Eq. (10), Fig. 3): for r = 1..rmax (rmax < nx, ny),
+ * S2_q[r-1] = <dq^2>, S4_q[r-1] = <dq^4> with dq = q(x + r e) - q(x) averaged over e = e_x, e_y
+ * (periodic) and all nodes of the planes; the flatness is S4 / S2^2. Host outputs of rmax values,
+ * any may be NULL. FP64 sums in a fixed order. Synchronises. Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+int lb_structure_functions(lb_ctx* ctx, int rmax, int z_lo, int z_hi, double* S2_uz, double* S4_uz,
+                           double* S2_T, double* S4_T);
+
 /* lb_save / lb_load -- checkpoint of (parameters, step count, populations in their storage
  * precision) to a raw binary file with a header and a 64-bit FNV-1a checksum of the payload.
  * lb_load requires a context created with the same grid and precision and replaces its state.

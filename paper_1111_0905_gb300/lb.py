@@ -22,7 +22,8 @@ _LIB_PATH = Path(__file__).resolve().parent / "libthermal_lbm.so"
 _lib = None
 
 # Names declared in include/lb.h.
-EXPORTS = ("lb_init", "lb_step", "lb_adjoint_step", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
+EXPORTS = ("lb_init", "lb_step", "lb_adjoint_step", "lb_profiles", "lb_histogram_T_rho",
+           "lb_structure_functions", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
            "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error",
            "lb_nusselt_fields_noalloc")
 NOALLOC_MAX_NZ = 8192
@@ -114,6 +115,12 @@ def load_library():
     lib.lb_strerror.restype = ctypes.c_char_p
     lib.lb_last_error.argtypes = [P]
     lib.lb_last_error.restype = ctypes.c_char_p
+    lib.lb_profiles.argtypes = [P, P, P, P]
+    lib.lb_profiles.restype = I
+    lib.lb_histogram_T_rho.argtypes = [P, I, I, I, D, D, I, D, D, P]
+    lib.lb_histogram_T_rho.restype = I
+    lib.lb_structure_functions.argtypes = [P, I, I, I, P, P, P, P]
+    lib.lb_structure_functions.restype = I
     lib.lb_adjoint_step.argtypes = [P, LL, I, DP, DP, DP, DP, P]
     lib.lb_adjoint_step.restype = I
     lib.lb_nusselt_fields_noalloc.argtypes = [P, P, P, I, I, I, D, D, D, D, D, P, P]
@@ -217,6 +224,27 @@ class Lattice:
                                              ctypes.byref(J), ctypes.byref(dTd), ctypes.byref(dTu),
                                              ctypes.byref(dG), _ptr(dT0)), "lb_adjoint_step")
         return {"J": J.value, "T_d": dTd.value, "T_u": dTu.value, "G": dG.value, "T0": dT0}
+
+    def profiles(self):
+        """(rho_z, T_z, PdivU_z): per-plane means of rho, T and P div(u)."""
+        out = [np.empty(self.params.nz, dtype=np.float64) for _ in range(3)]
+        self._check(self.lib.lb_profiles(self.ctx, *[_ptr(o) for o in out]), "lb_profiles")
+        return tuple(out)
+
+    def histogram_T_rho(self, z_lo, z_hi, nT, T_range, nrho, rho_range):
+        """uint64 counts [nT, nrho] of (T, rho) over planes [z_lo, z_hi)."""
+        counts = np.zeros((nT, nrho), dtype=np.uint64)
+        self._check(self.lib.lb_histogram_T_rho(self.ctx, z_lo, z_hi, nT, T_range[0], T_range[1],
+                                                nrho, rho_range[0], rho_range[1], _ptr(counts)),
+                    "lb_histogram_T_rho")
+        return counts
+
+    def structure_functions(self, rmax, z_lo, z_hi):
+        """dict of S2/S4 of u_z and T for horizontal increments r = 1..rmax."""
+        out = [np.empty(rmax, dtype=np.float64) for _ in range(4)]
+        self._check(self.lib.lb_structure_functions(self.ctx, rmax, z_lo, z_hi, *[_ptr(o) for o in out]),
+                    "lb_structure_functions")
+        return {"S2_uz": out[0], "S4_uz": out[1], "S2_T": out[2], "S4_T": out[3]}
 
     def moments(self, device: bool = False):
         """(rho, (ux, uy, uz), T) as numpy [nz, ny, nx] arrays, or torch CUDA tensors if device."""

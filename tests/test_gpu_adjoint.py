@@ -85,3 +85,48 @@ def test_adjoint_matches_central_differences_boiling_32(lblib, cuda):
     fd = (_J_gpu(p, rho, T + h * v, N) - _J_gpu(p, rho, T - h * v, N)) / (2 * h)
     ad = float((got["T0"] * v).sum())
     assert abs(fd - ad) <= 1e-4 * max(abs(fd), 1e-3), (fd, ad)
+
+
+def test_adjoint_of_the_fp32_form_matches_fp64(lblib, cuda):
+    """The FP32 form (FP32 forward states, FP64 adjoint arithmetic and accumulation) gives the
+    gradients of the FP64 form to the FP32 state error (1e-4 relative)."""
+    w = config.boiling_cell(24)
+    rho, T = w.fields()
+    g64 = lb.Lattice(w.params, rho, T).adjoint(100, 25, grad_T0=True)
+    p32 = lb.Params(**{**w.params.__dict__, "precision": lb.LB_FP32})
+    g32 = lb.Lattice(p32, rho, T).adjoint(100, 25, grad_T0=True)
+    assert abs(g32["J"] - g64["J"]) <= 1e-5 * abs(g64["J"])
+    for k in ("T_d", "T_u", "G"):
+        assert abs(g32[k] - g64[k]) <= 1e-4 * max(abs(g64[k]), 1e-3), (k, g32[k], g64[k])
+    assert np.abs(g32["T0"] - g64["T0"]).max() <= 1e-4 * np.abs(g64["T0"]).max()
+
+
+def test_adjoint_boiling_64_over_1000_steps(lblib, cuda):
+    """The 64^3 adjoint configuration: 1000 steps, checkpoints every 50; dJ/d(T_d, T_u, G)
+    against central differences (h = 1e-6) within 1e-4, and the cost against the forward run.
+    tau_nu = 1.25 and kappa = 0.15 (lambda = 0.3 in the g^eq positivity window) keep the
+    phase-separating cell bounded for the whole run (tau_nu = 1 breaks down after ~500 steps)."""
+    w = config.boiling_cell(64, kappa=0.15, tau_nu=1.25)
+    p = w.params
+    rho, T = w.fields()
+    N, K = 1000, 50
+    lat = lb.Lattice(p, rho, T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got = lat.adjoint(N, K)
+    t_adj = time.perf_counter() - t0
+    lat.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = _J_gpu(p, rho, T, N)
+    t_fwd = time.perf_counter() - t0
+    print(f"64^3 x 1000: J = {got['J']:.6f}, adjoint {t_adj:.2f} s vs forward {t_fwd:.2f} s "
+          f"({t_adj / t_fwd:.2f}x), grads {got['T_d']:.6e} {got['T_u']:.6e} {got['G']:.6e}")
+    assert abs(got["J"] - J) <= 1e-12 * abs(J)
+    h = 1e-6
+    for k in ("T_d", "T_u", "G"):
+        base = getattr(p, k)
+        fd = (_J_gpu(lb.Params(**{**p.__dict__, k: base + h}), rho, T, N)
+              - _J_gpu(lb.Params(**{**p.__dict__, k: base - h}), rho, T, N)) / (2 * h)
+        print(f"  {k}: adjoint {got[k]:.8e}, central difference {fd:.8e}")
+        assert abs(fd - got[k]) <= 1e-4 * max(abs(fd), 1e-3), (k, fd, got[k])

@@ -1,0 +1,55 @@
+"""Parity of the statistics entry points (lb_profiles, lb_histogram_T_rho,
+lb_structure_functions) with the oracle's, on the same evolved boiling cell."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import analysis, lbm
+from paper_1111_0905_gb300 import config, lb
+from helpers import oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def evolved(lblib, cuda):
+    w = config.boiling_cell(24, nz=20, ny=16)
+    rho, T = w.fields()
+    lat = lb.Lattice(w.params, rho, T)
+    lat.step(60)
+    f, g, op, _ = oracle_run(w.params, rho, T, 60)
+    yield lat, f, g, op
+    lat.close()
+
+
+def test_profiles_match_oracle(evolved):
+    lat, f, g, op = evolved
+    r_z, T_z, PD_z = lat.profiles()
+    r_o, T_o, PD_o = (t.numpy() for t in analysis.profiles(f, g, op))
+    assert np.abs(r_z - r_o).max() <= 1e-12 * np.abs(r_o).max()
+    assert np.abs(T_z - T_o).max() <= 1e-12 * np.abs(T_o).max()
+    assert np.abs(PD_z - PD_o).max() <= 1e-10 * max(np.abs(PD_o).max(), 1e-12)
+
+
+def test_histogram_matches_oracle(evolved):
+    lat, f, g, op = evolved
+    rho_o, u_o, T_o = (x.numpy() if hasattr(x, "numpy") else x for x in lbm.moments_out(f, g, op))
+    rng_T, rng_r, nT, nr = (0.30, 0.38), (0.4, 2.0), 16, 24
+    got = lat.histogram_T_rho(2, 18, nT, rng_T, nr, rng_r)
+    ref = analysis.histogram_T_rho(rho_o, T_o, 2, 18, nT, rng_T, nr, rng_r)
+    # values within 1e-10 (relative) of a bin edge may fall on either side between the two codes
+    Tn = (T_o[2:18] - rng_T[0]) / (rng_T[1] - rng_T[0]) * nT
+    rn = (rho_o[2:18] - rng_r[0]) / (rng_r[1] - rng_r[0]) * nr
+    near = int(np.sum((np.abs(Tn - np.round(Tn)) < 1e-9) | (np.abs(rn - np.round(rn)) < 1e-9)))
+    assert got.sum() == ref.sum() or near > 0
+    assert int(np.abs(got.astype(np.int64) - ref.astype(np.int64)).sum()) <= 2 * near
+    assert ref.sum() > 0.9 * 16 * 16 * 24
+
+
+def test_structure_functions_match_oracle(evolved):
+    lat, f, g, op = evolved
+    rho_o, u_o, T_o = lbm.moments_out(f, g, op)
+    got = lat.structure_functions(10, 3, 17)
+    ref = analysis.structure_functions(u_o[2].numpy(), T_o.numpy(), 10, 3, 17)
+    for k in ref:
+        assert np.abs(got[k] - ref[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k

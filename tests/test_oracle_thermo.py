@@ -118,9 +118,13 @@ def test_linear_stability_of_the_workload_parameters():
     vapour, the boiling liquid and the compressed liquid."""
     from paper_1111_0905_gb300 import config
     k_single = config.single_phase_cell(128).params.kappa
-    k_boil = config.paper_scale_cell(256).params.kappa
-    for rho0, kappa in [(2.3, k_single), (0.57, k_boil), (1.79, k_boil), (1.3, 0.05)]:
-        assert _spectral_radius(rho0, 1.0, 1.0, kappa, (2, 2, 2)) < 1 + 1e-9
+    pb = config.paper_scale_cell(256).params
+    for rho0 in (2.3, 2.25):
+        assert _spectral_radius(rho0, 1.0, 1.0, k_single, (2, 2, 2)) < 1 + 1e-9
+    for rho0 in (0.57, 1.0, 1.5, 1.79):
+        assert _spectral_radius(rho0, pb.tau_nu, pb.tau_kappa, pb.kappa, (2, 2, 2)) < 1 + 1e-9
+        assert _spectral_radius(rho0, 1.25, 1.0, 0.15, (2, 2, 2)) < 1 + 1e-9
+    assert _spectral_radius(1.3, 1.0, 1.0, 0.05, (2, 2, 2)) < 1 + 1e-9
 
 
 def test_small_tau_is_linearly_unstable():
