@@ -40,14 +40,18 @@ ERR_STEPS = 200
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the fused step
 # kernel from an ncu capture, keyed by the hash of the kernel sources it was taken on; it is
 # reported as null when the sources have changed since.
-TRAFFIC = {"src_hash": "0834d8f325af8226",
+TRAFFIC = {"src_hash": "e4a2e664603db00a",
            "bytes_per_launch": {"f32": 337872384 + 275959552, "fp16dev": 166958592 + 118238208}}
 
 
+STEP_KERNEL_SOURCES = ("lb_kernels.cuh", "lb_launch.cuh", "lb_prec_f32.cu", "lb_prec_f16.cu")
+
+
 def kernel_src_hash() -> str:
+    """Hash of the sources the step kernels are compiled from (the FP32 and FP16 forms)."""
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_1111_0905_gb300" / "csrc").glob("*.cu*")):
-        h.update(p.read_bytes())
+    for name in STEP_KERNEL_SOURCES:
+        h.update((ROOT / "paper_1111_0905_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -217,6 +221,7 @@ def run_ours(args):
         ms = time_steps(lat, K, W, sampler)
         if sampler is not None:
             clock_summary = sampler.summary()
+        health = lat.diagnostics()          # outside the timed region: the state stayed physical
         ms = max_over_ranks(ms)
         per_step = ms / K
         lat.close()
@@ -230,6 +235,9 @@ def run_ours(args):
         bytes_step = 2 * 2 * Q * N * STORE_BYTES[form]
         glups_rank = N / (per_step * 1e-3) / 1e9
         results[form] = {"glups": glups_rank * ws, "ms_per_step": per_step, "steps": K,
+                         "state_after": {"min_rho": float(health["min_rho"]),
+                                         "min_T": float(health["min_T"]),
+                                         "nonfinite": int(health["nonfinite"])},
                          "hbm_gbs_algorithmic": bytes_step / (per_step * 1e-3) / 1e9,
                          "hbm_frac": bytes_step / (per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
                          "bytes_per_node": 4 * Q * STORE_BYTES[form]}
