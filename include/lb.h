@@ -165,6 +165,13 @@ int lb_load(lb_ctx* ctx, const char* path);
 /* lb_step_count -- number of steps taken since lb_init (or restored by lb_load); -1 if ctx is NULL. */
 long long lb_step_count(const lb_ctx* ctx);
 
+/* lb_launch_info -- how the context's step kernel is launched (launch metadata for performance
+ * reports; the paper has no counterpart). Host output of 6 ints: out[0], out[1] = grid (column
+ * tiles, z chunks), out[2] = threads per CTA, out[3] = dynamic shared memory bytes per CTA,
+ * out[4] = CTAs resident per SM as the CUDA occupancy calculator reports it, out[5] = registers
+ * per thread. Errors: LB_EINVAL (NULL argument), LB_ECUDA. */
+int lb_launch_info(lb_ctx* ctx, int* out);
+
 /* lb_free -- release the context and its device memory (synchronises its stream). NULL is a no-op. */
 void lb_free(lb_ctx* ctx);
 

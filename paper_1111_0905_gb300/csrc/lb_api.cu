@@ -195,6 +195,16 @@ const char* lb_last_error(const lb_ctx* c) { return c ? c->err.c_str() : kNullCt
 
 long long lb_step_count(const lb_ctx* c) { return c ? c->step : -1; }
 
+int lb_launch_info(lb_ctx* c, int* out) {
+  if (!c || !out) return LB_EINVAL;
+  int k[4] = {0, 0, 0, 0};
+  LB_CU(c, c->ops->info(c->by, k));
+  const dim3 grid = fused_grid(c);
+  out[0] = (int)grid.x; out[1] = (int)grid.y;
+  out[2] = k[0]; out[3] = k[1]; out[4] = k[2]; out[5] = k[3];
+  return LB_OK;
+}
+
 int lb_init(const lb_params* params, const double* rho_init, const double* T_init,
             int init_on_device, void* cuda_stream, lb_ctx** out) {
   if (!out) return LB_EINVAL;
@@ -227,18 +237,34 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   c->tiles_x = (p.nx + BX - 1) / BX;
   c->tiles_y = (p.ny + by - 1) / by;
   c->ntiles = c->tiles_x * c->tiles_y;
-  if (p.z_chunk > 0) {
-    c->zc = p.z_chunk < p.nz ? p.z_chunk : p.nz;
-  } else {
-    // 32 planes per chunk: the 4 prologue planes of a chunk cost 1/8 extra ring pulls, and the
-    // 128^3 and 256^3 cells keep every SM busy (measured best of 8..256)
-    c->zc = p.nz < 32 ? p.nz : 32;
-  }
-  c->nchunks = (p.nz + c->zc - 1) / c->zc;
 
   auto bail = [&](int code) { free_all(c); delete c; return code; };
   if (cudaGetDevice(&c->device) != cudaSuccess) return bail(LB_ECUDA);
   if (ops->prepare() != cudaSuccess) return bail(LB_ECUDA);
+  if (p.z_chunk > 0) {
+    c->zc = p.z_chunk < p.nz ? p.z_chunk : p.nz;
+  } else {
+    // Planes per chunk: each chunk adds 4 prologue planes (M stages without collisions) and the
+    // CTAs run in waves of (resident CTAs per SM) x SMs, so a launch takes about
+    // ceil(CTAs / slots) * (zc + 4) plane-steps. Take the chunk count (zc from 8 to 128, or nz)
+    // that minimises it; ties go to the larger chunk.
+    int k[4] = {0, 0, 0, 0}, sms = 0;
+    if (ops->info(by, k) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+      return bail(LB_ECUDA);
+    const long long slots = (long long)(k[2] > 0 ? k[2] : 1) * (sms > 0 ? sms : 1);
+    c->zc = p.nz;
+    long long best = -1;
+    for (int nch = 1; nch <= p.nz; ++nch) {
+      const int zc = (p.nz + nch - 1) / nch;
+      if (zc > 128) continue;
+      if (zc < 8 && nch > 1) break;
+      const long long ctas = (long long)c->ntiles * ((p.nz + zc - 1) / zc);
+      const long long cost = ((ctas + slots - 1) / slots) * (zc + 4);
+      if (best < 0 || cost < best) { best = cost; c->zc = zc; }
+    }
+  }
+  c->nchunks = (p.nz + c->zc - 1) / c->zc;
 
   // validate the initial fields and form their means on the device (fixed-order sums)
   const double* d_rho = rho_init;

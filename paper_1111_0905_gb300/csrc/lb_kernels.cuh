@@ -14,8 +14,8 @@
 // j in shared memory; (U) for plane p-1 forms the force F and the physical velocity
 // u = (j + F/2)/rho on the tile plus a radius-1 ring; (C) for plane p-2 it pulls f and g of the
 // tile, takes div(u) from the three u planes and collides. Shared memory holds rolling windows
-// of 3 psi planes, 2 rho/j planes, 3 u planes and 2 F planes, so the only HBM traffic is the
-// populations (the ring pulls hit L1/L2).
+// of psi and rho/j planes (3 or 4 deep), 3 u planes and 2 F planes, so the only HBM traffic is
+// the populations (the ring pulls hit L1/L2). One or two barriers per plane.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -195,20 +195,28 @@ template <int BY> struct Geo {
   static constexpr int TXY = BX * BY;
   static constexpr int MAXM = (RXY + NT - 1) / NT;
   static constexpr int NHALO = 2 * BX + 2 * BY;
-  // R units: psi[3][RXY], rj[3][5][HXY] (rho, 1/rho, jx, jy, jz), u[3][3][HXY], F[2][3][TXY];
-  // then either the pulled-f cache of the tile, fc[3][Q][TXY] in storage units S, or (STG) the
+  // Depth D of the psi, rho/j and f-cache rings. With D = 4 the C stage of one z-iteration and
+  // the M stage of the next need no barrier between them (the next M stage refills the slot of
+  // plane p-3, last read before this iteration's barrier); with D = 3 a trailing barrier ends
+  // each iteration. Measured: 4 for the 16-bit forms, 3 for FP32 (smaller shared-memory window,
+  // larger L1 share) and FP64 (shared memory).
+  template <class S> static constexpr int depth() { return sizeof(S) == 2 ? 4 : 3; }
+  // R units: psi[D][RXY], rj[D][5][HXY] (rho, 1/rho, jx, jy, jz), u[3][3][HXY], F[2][3][TXY];
+  // then either the pulled-f cache of the tile, fc[D][Q][TXY] in storage units S, or (STG) the
   // stage of the collision's pulled f and g, stg[2][Q][TXY] in 4-byte words.
-  template <class R> static constexpr size_t r_count() {
-    return (size_t)(3 * RXY + 15 * HXY + 9 * HXY + 6 * TXY);
+  template <class S> static constexpr size_t r_count() {
+    return (size_t)(depth<S>() * (RXY + 5 * HXY) + 9 * HXY + 6 * TXY);
   }
   template <class S, class R, bool STG> static constexpr size_t smem_bytes() {
-    return sizeof(R) * r_count<R>() +
-           (STG ? sizeof(uint32_t) * (size_t)(2 * Q * TXY) : sizeof(S) * (size_t)(3 * Q * TXY));
+    return sizeof(R) * r_count<S>() +
+           (STG ? sizeof(uint32_t) * (size_t)(2 * Q * TXY) : sizeof(S) * (size_t)(depth<S>() * Q * TXY));
   }
 };
 
 __device__ __forceinline__ int slot3(int p) { return (p + 6) % 3; }
 __device__ __forceinline__ int slot2(int p) { return (p + 6) & 1; }
+// slot of plane p in a ring of depth D (3 or 4); p >= -6
+template <int D> __device__ __forceinline__ int ring(int p) { return D == 4 ? ((p + 8) & 3) : (p + 6) % 3; }
 
 template <class R> __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
@@ -294,13 +302,14 @@ lb_fused_kernel(const KArgs a) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool STG = std::is_same<S, float>::value && TLBM_STAGE;
-  R* psi_s = reinterpret_cast<R*>(smem_raw);  // [3][RXY]
-  R* rj_s = psi_s + 3 * RXY;                  // [3][5][HXY]  rho, 1/rho, jx, jy, jz
-  R* u_s = rj_s + 15 * HXY;                   // [3][3][HXY]  physical velocity
+  constexpr int D = GE::template depth<S>();
+  R* psi_s = reinterpret_cast<R*>(smem_raw);  // [D][RXY]
+  R* rj_s = psi_s + D * RXY;                  // [D][5][HXY]  rho, 1/rho, jx, jy, jz
+  R* u_s = rj_s + D * 5 * HXY;                // [3][3][HXY]  physical velocity
   R* F_s = u_s + 9 * HXY;                     // [2][3][TXY]  force on the tile
   // FP32 stages the collision's pulled f and g asynchronously; FP64 and the 16-bit forms keep
   // the f cache (measured faster for them) and pull g directly.
-  S* fc_s = reinterpret_cast<S*>(F_s + 6 * TXY);                 // [3][Q][TXY] (not STG)
+  S* fc_s = reinterpret_cast<S*>(F_s + 6 * TXY);                 // [D][Q][TXY] (not STG)
   uint32_t* stg_s = reinterpret_cast<uint32_t*>(F_s + 6 * TXY);  // [2][Q][TXY] (STG)
 
   const S* __restrict__ fin = static_cast<const S*>(a.fin);
@@ -372,7 +381,7 @@ lb_fused_kernel(const KArgs a) {
       const int pz = mirror_z(p, nz);
       const bool wallp = (pz == 0 || pz == nz - 1);
       const bool real = (p == pz);
-      const int s3 = slot3(p);
+      const int s3 = ring<D>(p);
 #pragma unroll
       for (int i = 0; i < MAXM; ++i) {
         const int k = tid + i * NT;
@@ -405,10 +414,10 @@ lb_fused_kernel(const KArgs a) {
     {
       const int q = p - 1;
       if (q >= z0 - 1 && q <= z1 && q >= 0 && q < nz) {
-        const R* pm = psi_s + slot3(q - 1) * RXY;
-        const R* p0 = psi_s + slot3(q) * RXY;
-        const R* pp = psi_s + slot3(q + 1) * RXY;
-        const R* rj = rj_s + slot3(q) * 5 * HXY;
+        const R* pm = psi_s + ring<D>(q - 1) * RXY;
+        const R* p0 = psi_s + ring<D>(q) * RXY;
+        const R* pp = psi_s + ring<D>(q + 1) * RXY;
+        const R* rj = rj_s + ring<D>(q) * 5 * HXY;
         R* us = u_s + slot3(q) * 3 * HXY;
         R* Fs = F_s + slot2(q) * 3 * TXY;
         auto unode = [&](int xr, int yr, bool on_tile) {
@@ -438,7 +447,8 @@ lb_fused_kernel(const KArgs a) {
         if (has_halo) unode(hx, hy, false);
       }
     }
-    __syncthreads();
+    // No barrier before C: of what this U stage writes, C reads u of plane p-1 and F only at the
+    // thread's own node (written by itself); its ring reads are of planes finished one barrier ago.
     // ---------------- C: collide plane z = p-2 ----------------
     // moments-mode partials of this thread's node (neutral values when it has none)
     double d_conv = 0.0, d_T = 0.0, d_rho = 0.0, d_E = 0.0, d_mr = 1e300, d_mT = 1e300, d_bad = 0.0;
@@ -461,13 +471,13 @@ lb_fused_kernel(const KArgs a) {
         else pull_raw<S, false>(gr, gin, N, z, nz, plane, ccol, crow);
 #pragma unroll
         for (int l = 0; l < Q; ++l) g[l] = cvt<S, R>(gr[l]);
-        const S* fc = fc_s + slot3(z) * Q * TXY + t;
+        const S* fc = fc_s + ring<D>(z) * Q * TXY + t;
 #pragma unroll
         for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fc[l * TXY]);
       }
       if (wallz) g_wall_fix<S, R>(g, fin, (int)N, (int)own, z, nz, rho0, T0, Td, Tu, lam);
       const int cc = (ty + 1) * HX + (tx + 1);
-      const R* rjc = rj_s + slot3(z) * 5 * HXY + cc;
+      const R* rjc = rj_s + ring<D>(z) * 5 * HXY + cc;
       const R rho = rjc[0], inv = rjc[HXY];
       const R jx = rjc[2 * HXY], jy = rjc[3 * HXY], jz = rjc[4 * HXY];
       const R drho = rho - rho0;
@@ -572,8 +582,9 @@ lb_fused_kernel(const KArgs a) {
         }
       }
     }
-    // the next M stage refills the ring slots that this C stage read
-    __syncthreads();
+    // With D = 3 the next M stage refills the psi slot that this U stage read and the rho/j
+    // (and f-cache) slot that this C stage read.
+    if (D == 3) __syncthreads();
   }
 }
 

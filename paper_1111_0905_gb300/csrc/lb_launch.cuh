@@ -13,6 +13,9 @@ struct PrecOps {
   cudaError_t (*init)(const KArgs&, const double*, const double*, cudaStream_t);
   cudaError_t (*pops)(const KArgs&, double*, double*, cudaStream_t);
   bool (*tile_ok)(int by);    // whether the tile height's shared-memory window fits a CTA
+  // launch description of the step kernel for a tile height: out = {threads per CTA, dynamic
+  // shared memory bytes, resident CTAs per SM, registers per thread}
+  cudaError_t (*info)(int by, int out[4]);
 };
 
 extern const PrecOps kOpsF64, kOpsF32, kOpsBF16, kOpsF16;
@@ -41,6 +44,27 @@ template <class S> struct OpsImpl {
     if ((e = attr<4, MODE_MOMENTS>()) != cudaSuccess) return e;
     if ((e = attr<8, MODE_MOMENTS>()) != cudaSuccess) return e;
     return attr<16, MODE_MOMENTS>();
+  }
+  template <int BY> static cudaError_t info_by(int out[4]) {
+    if constexpr (!fits<BY>()) {
+      return cudaErrorInvalidConfiguration;
+    } else {
+      cudaFuncAttributes fa;
+      cudaError_t e = cudaFuncGetAttributes(&fa, lb_fused_kernel<S, BY, MODE_STEP>);
+      if (e != cudaSuccess) return e;
+      int n = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lb_fused_kernel<S, BY, MODE_STEP>, BX * BY,
+                                                        smem<BY>());
+      if (e != cudaSuccess) return e;
+      out[0] = BX * BY; out[1] = (int)smem<BY>(); out[2] = n; out[3] = fa.numRegs;
+      return cudaSuccess;
+    }
+  }
+  static cudaError_t info(int by, int out[4]) {
+    if (by == 4) return info_by<4>(out);
+    if (by == 8) return info_by<8>(out);
+    if (by == 16) return info_by<16>(out);
+    return cudaErrorInvalidValue;
   }
   static bool tile_ok(int by) {
     return (by == 4 && fits<4>()) || (by == 8 && fits<8>()) || (by == 16 && fits<16>());

@@ -4,5 +4,5 @@
 namespace tlbm {
 const PrecOps kOpsF64 = {sizeof(double), 0, &OpsImpl<double>::prepare, &OpsImpl<double>::fused,
                     &OpsImpl<double>::init, &OpsImpl<double>::pops,
-                    &OpsImpl<double>::tile_ok};
+                    &OpsImpl<double>::tile_ok, &OpsImpl<double>::info};
 }  // namespace tlbm

@@ -25,7 +25,7 @@ _lib = None
 EXPORTS = ("lb_init", "lb_step", "lb_adjoint_step", "lb_profiles", "lb_histogram_T_rho",
            "lb_structure_functions", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
            "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error",
-           "lb_nusselt_fields_noalloc")
+           "lb_nusselt_fields_noalloc", "lb_launch_info")
 NOALLOC_MAX_NZ = 8192
 
 
@@ -125,6 +125,8 @@ def load_library():
     lib.lb_adjoint_step.restype = I
     lib.lb_nusselt_fields_noalloc.argtypes = [P, P, P, I, I, I, D, D, D, D, D, P, P]
     lib.lb_nusselt_fields_noalloc.restype = I
+    lib.lb_launch_info.argtypes = [P, P]
+    lib.lb_launch_info.restype = I
     _lib = lib
     return lib
 
@@ -214,6 +216,13 @@ class Lattice:
     @property
     def step_count(self) -> int:
         return int(self.lib.lb_step_count(self.ctx))
+
+    def launch_info(self) -> dict:
+        """lb_launch_info: grid, threads and shared memory per CTA, resident CTAs per SM, registers."""
+        out = (ctypes.c_int * 6)()
+        self._check(self.lib.lb_launch_info(self.ctx, out), "lb_launch_info")
+        return {"grid": [out[0], out[1]], "threads_per_cta": out[2], "smem_bytes": out[3],
+                "ctas_per_sm": out[4], "registers": out[5]}
 
     def adjoint(self, nsteps: int, checkpoint_every: int = 50, grad_T0: bool = False) -> dict:
         """lb_adjoint_step: J = time-averaged Nu over the next nsteps steps and dJ/d(T_d, T_u, G)

@@ -65,6 +65,7 @@ def test_library_builds_and_exports_every_declared_symbol(lblib):
         assert hasattr(lblib, name)
     assert lblib.lb_strerror(-4).decode().startswith("non-physical")
     assert lblib.lb_step_count(None) == -1
+    assert lblib.lb_launch_info(None, None) == -1   # LB_EINVAL, no device needed
 
 
 def test_lb_params_layout_matches_the_c_header(tmp_path):
