@@ -40,8 +40,8 @@ ERR_STEPS = 200
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the fused step
 # kernel from an ncu capture, keyed by the hash of the kernel sources it was taken on; it is
 # reported as null when the sources have changed since.
-TRAFFIC = {"src_hash": "e4a2e664603db00a",
-           "bytes_per_launch": {"f32": 337872384 + 275959552, "fp16dev": 166958592 + 118238208}}
+TRAFFIC = {"src_hash": "bc73714fa6a9fc19",
+           "bytes_per_launch": {"f32": 337839360 + 276063744, "fp16dev": 166898432 + 117961984}}
 
 
 STEP_KERNEL_SOURCES = ("lb_kernels.cuh", "lb_launch.cuh", "lb_prec_f32.cu", "lb_prec_f16.cu")
@@ -148,7 +148,8 @@ def config_dict(w, form: str) -> dict:
     N = p.nx * p.ny * p.nz
     in_bytes = 2 * Q * N * STORE_BYTES[form]
     return {"workload": f"single-phase thermal convection cell {p.nx}x{p.ny}x{p.nz} "
-                        f"(rho=2.30, Pr=9, tau_nu=tau_kappa=1, Ra=0.5*Ra_max), {form} form",
+                        f"(rho=2.30, Pr=9, tau_nu={p.tau_nu:g}, tau_kappa={p.tau_kappa:g}, "
+                        f"Ra=0.5*Ra_max), {form} form",
             "grid": [p.nx, p.ny, p.nz], "nodes": N, "form": form,
             "l2": f"inputs larger than L2: {in_bytes / 1e6:.0f} MB of populations read per step "
                   f"> 129 MB L2; no flush",
@@ -210,6 +211,7 @@ def run_ours(args):
         rho_d = torch.from_numpy(rho).cuda()
         T_d = torch.from_numpy(T).cuda()
         lat = lb.Lattice(p, rho_d, T_d)
+        launch = lat.launch_info()
         K = args.steps if form == main_form else min(args.steps, 2000)
         W = args.warmup
         uuid = None
@@ -240,7 +242,7 @@ def run_ours(args):
                                          "nonfinite": int(health["nonfinite"])},
                          "hbm_gbs_algorithmic": bytes_step / (per_step * 1e-3) / 1e9,
                          "hbm_frac": bytes_step / (per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                         "bytes_per_node": 4 * Q * STORE_BYTES[form]}
+                         "bytes_per_node": 4 * Q * STORE_BYTES[form], "launch": launch}
         del rho_d, T_d
         torch.cuda.empty_cache()
 
@@ -328,6 +330,7 @@ def size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
             N = p.nx * p.ny * p.nz
             rho, T = w.fields()
             lat = lb.Lattice(p, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+            launch = lat.launch_info()
             del rho, T
             lat.step(10)
             torch.cuda.synchronize()
@@ -345,7 +348,7 @@ def size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
             bytes_step = 4 * Q * STORE_BYTES[form] * N
             out[f"{n}^3_{form}"] = {"glups": N / (ms * 1e-3) / 1e9 * ws, "ms_per_step": ms,
                                     "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                                    "workload": w.name}
+                                    "workload": w.name, "launch": launch}
     return out
 
 
@@ -364,13 +367,15 @@ def _oracle_sample(side: int):
 
 
 def cpu_baseline(args) -> dict:
-    """FP64 oracle timed on the host cores on a bounded sample: 6 steps of the full 128^3 cell."""
+    """FP64 oracle timed on the host cores on a bounded sample of the full 128^3 cell: as many
+    steps as take about 15 s (6 to 100), after one warm-up step."""
     import torch
     from oracle import lbm
     f, g, op = _oracle_sample(128)
-    f, g = lbm.step(f, g, op)  # warm-up
     t0 = time.perf_counter()
-    n = 6
+    f, g = lbm.step(f, g, op)  # warm-up, also sizes the sample
+    n = max(6, min(100, int(15.0 / max(time.perf_counter() - t0, 1e-3))))
+    t0 = time.perf_counter()
     for _ in range(n):
         f, g = lbm.step(f, g, op)
     dt = time.perf_counter() - t0

@@ -22,40 +22,59 @@ namespace tlbm {
 // Diagnostics finalisation: per-plane sums over tiles in a fixed order, then Nu(z) of Eq. (4)
 // (normalised by kappa (T_d - T_u)/nz) and global min/sums. out layout:
 // [0, nz) Nu(z); nz: Nu_mean; nz+1: min rho; nz+2: min T; nz+3: non-finite count;
-// nz+4: sum rho; nz+5: sum rho T. If acc != null, acc[0] += Nu_mean, acc[1] += 1.
-__global__ void lb_diag_finalize(const double* __restrict__ part, int nz, int ntiles, int nxy,
-                                 double kappa, double T_d, double T_u, double* __restrict__ out,
-                                 double* __restrict__ acc) {
-  extern __shared__ double sh[];  // [nz] conv sums, [nz] T sums
-  double* sconv = sh;
-  double* sT = sh + nz;
-  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+// nz+4: sum rho; nz+5: sum rho T; [nz+8, 2nz+8) per-plane T sums (scratch).
+// If acc != null, acc[0] += Nu_mean, acc[1] += 1.
+__global__ void __launch_bounds__(1024) lb_diag_finalize(const double* __restrict__ part, int nz, int ntiles,
+                                                         int nxy, double kappa, double T_d, double T_u,
+                                                         double* __restrict__ out, double* __restrict__ acc) {
+  // One CTA of 1024 threads; every sum has a fixed assignment of terms to lanes and a fixed
+  // combination tree, so the result does not depend on timing.
+  __shared__ double red[6][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  double* sT = out + nz + 8;   // per-plane T sums (scratch after the result slots)
+  // per-plane sums of the convective flux and of T over the tiles: one warp per plane
+  for (int z = warp; z < nz; z += nwarp) {
     double c = 0.0, t = 0.0;
-    for (int k = 0; k < ntiles; ++k) {
+    for (int k = lane; k < ntiles; k += 32) {
       c += part[((size_t)z * ntiles + k) * NPART + 0];
       t += part[((size_t)z * ntiles + k) * NPART + 1];
     }
-    sconv[z] = c; sT[z] = t;
+    c = warp_sum(c);
+    t = warp_sum(t);
+    if (lane == 0) { out[z] = c; sT[z] = t; }
   }
   __syncthreads();
   const double norm = kappa * (T_d - T_u) / nz;
+  double s = 0.0;
   for (int z = threadIdx.x; z < nz; z += blockDim.x) {
     const double Tp = (z + 1 < nz) ? sT[z + 1] : 2.0 * T_u * nxy - sT[nz - 1];
     const double Tm = (z - 1 >= 0) ? sT[z - 1] : 2.0 * T_d * nxy - sT[0];
-    const double flux = (sconv[z] - kappa * 0.5 * (Tp - Tm)) / nxy;
+    const double flux = (out[z] - kappa * 0.5 * (Tp - Tm)) / nxy;
     out[z] = flux / norm;
+    s += out[z];
+  }
+  // global sums and minima over every (plane, tile) partial
+  double sr = 0.0, sE = 0.0, mr = 1e300, mT = 1e300, bad = 0.0;
+  for (size_t k = threadIdx.x; k < (size_t)nz * ntiles; k += blockDim.x) {
+    const double* p = part + k * NPART;
+    sr += p[2]; sE += p[3]; mr = fmin(mr, p[4]); mT = fmin(mT, p[5]); bad += p[6];
+  }
+  s = warp_sum(s); sr = warp_sum(sr); sE = warp_sum(sE); bad = warp_sum(bad);
+  mr = warp_min(mr); mT = warp_min(mT);
+  if (lane == 0) {
+    red[0][warp] = s; red[1][warp] = sr; red[2][warp] = sE; red[3][warp] = bad;
+    red[4][warp] = mr; red[5][warp] = mT;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0, mr = 1e300, mT = 1e300, bad = 0.0, sr = 0.0, sE = 0.0;
-    for (int z = 0; z < nz; ++z) s += out[z];
-    for (size_t k = 0; k < (size_t)nz * ntiles; ++k) {
-      const double* p = part + k * NPART;
-      sr += p[2]; sE += p[3]; mr = fmin(mr, p[4]); mT = fmin(mT, p[5]); bad += p[6];
+    double a[6] = {red[0][0], red[1][0], red[2][0], red[3][0], red[4][0], red[5][0]};
+    for (int w = 1; w < nwarp; ++w) {
+      for (int k = 0; k < 4; ++k) a[k] += red[k][w];
+      a[4] = fmin(a[4], red[4][w]); a[5] = fmin(a[5], red[5][w]);
     }
-    const double mean = s / nz;
-    out[nz] = mean; out[nz + 1] = mr; out[nz + 2] = mT; out[nz + 3] = bad;
-    out[nz + 4] = sr; out[nz + 5] = sE;
+    const double mean = a[0] / nz;
+    out[nz] = mean; out[nz + 1] = a[4]; out[nz + 2] = a[5]; out[nz + 3] = a[3];
+    out[nz + 4] = a[1]; out[nz + 5] = a[2];
     if (acc) { acc[0] += mean; acc[1] += 1.0; }
   }
 }
@@ -148,7 +167,7 @@ int run_diag_acc(lb_ctx* c, double* acc) {
   a.part = c->part;
   LB_CU(c, c->ops->fused(a, MODE_MOMENTS, c->by, fused_grid(c), c->stream));
   const int nz = c->p.nz;
-  lb_diag_finalize<<<1, 256, 2 * nz * sizeof(double), c->stream>>>(
+  lb_diag_finalize<<<1, 1024, 0, c->stream>>>(
       c->part, nz, c->ntiles, c->p.nx * c->p.ny, c->p.kappa, c->p.T_d, c->p.T_u, c->diag, acc);
   LB_CU(c, cudaGetLastError());
   return LB_OK;
@@ -308,7 +327,7 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
     }
   }
   if (cudaMalloc(&c->part, (size_t)p.nz * c->ntiles * NPART * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->diag, (size_t)(p.nz + 8) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->diag, (size_t)(2 * p.nz + 8) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->nu_acc, 2 * sizeof(double)) != cudaSuccess) {
     cudaFree(staging);
     return bail(LB_ENOMEM);

@@ -130,3 +130,31 @@ def test_adjoint_boiling_64_over_1000_steps(lblib, cuda):
               - _J_gpu(lb.Params(**{**p.__dict__, k: base - h}), rho, T, N)) / (2 * h)
         print(f"  {k}: adjoint {got[k]:.8e}, central difference {fd:.8e}")
         assert abs(fd - got[k]) <= 1e-4 * max(abs(fd), 1e-3), (k, fd, got[k])
+
+
+@pytest.mark.parametrize("device", ["cpu", "cuda"])
+def test_autograd_function_matches_the_oracle_gradient(lblib, cuda, device):
+    """torch.autograd binding: J.backward() through NusseltObjective gives the oracle's exact
+    gradient (PyTorch autograd through the plain FP64 steps) in T_d, T_u, G and T0, with the
+    initial fields on the host or on the GPU; without gradients the forward pass (lb_step with
+    a Nu sample per step) gives the same J."""
+    from paper_1111_0905_gb300.autograd import nusselt_objective
+    w = config.boiling_cell(8, nz=7, ny=6)
+    rho, T = w.fields()
+    nsteps, K = 12, 5
+    Td = torch.tensor(w.params.T_d, dtype=DT, requires_grad=True)
+    Tu = torch.tensor(w.params.T_u, dtype=DT, requires_grad=True)
+    G = torch.tensor(w.params.G, dtype=DT, requires_grad=True)
+    T0 = torch.from_numpy(T).to(device).requires_grad_(True)
+    J = nusselt_objective(Td, Tu, G, T0, rho, w.params, nsteps, K)
+    (2.0 * J).backward()
+    ref = _oracle_grad(w.params, rho, T, nsteps)
+    assert abs(J.item() - ref["J"]) <= 1e-11 * max(1.0, abs(ref["J"]))
+    for k, t in (("T_d", Td), ("T_u", Tu), ("G", G)):
+        assert abs(t.grad.item() - 2.0 * ref[k]) <= 1e-9 * max(1.0, abs(ref[k])), k
+    assert T0.grad.device.type == device
+    scale = np.abs(ref["T0"]).max()
+    assert np.abs(T0.grad.cpu().numpy() - 2.0 * ref["T0"]).max() <= 2e-9 * scale
+    J0 = nusselt_objective(Td.detach(), Tu.detach(), G.detach(), T0.detach(), rho, w.params, nsteps, K)
+    assert not J0.requires_grad
+    assert abs(J0.item() - J.item()) <= 1e-12 * max(1.0, abs(J.item()))

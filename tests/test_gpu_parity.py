@@ -240,3 +240,65 @@ def test_device_pointers_and_stream(lblib, cuda):
     rb, ub, Tb = b.moments()
     assert np.array_equal(ra.cpu().numpy(), rb) and np.array_equal(Ta.cpu().numpy(), Tb)
     a.close(); b.close()
+
+
+SHAPES = [(8, 0), (8, 5), (4, 7), (16, 23), (4, 1)]
+
+
+@pytest.mark.parametrize("prec", [lb.LB_FP64, lb.LB_FP32, lb.LB_BF16_DEV, lb.LB_FP16_DEV])
+def test_launch_shape_does_not_change_the_result(lblib, cuda, prec):
+    """Every node's arithmetic is the same whatever the tile height and z chunk (chunk prologues
+    recompute their planes identically): populations after 30 steps of a ragged boiling cell
+    are bitwise equal across launch shapes, in every form."""
+    w = config.boiling_cell(40, nz=23, ny=19, precision=prec)
+    rho, T = w.fields()
+    ref = None
+    for by, zc in SHAPES:
+        if by == 16 and prec == lb.LB_FP64:
+            continue
+        p = w.params
+        p.tile_y, p.z_chunk = by, zc
+        lat = lb.Lattice(p, rho, T)
+        info = lat.launch_info()
+        assert info["threads_per_cta"] == 32 * by
+        if zc:
+            assert info["grid"][1] == -(-23 // zc)
+        lat.step(30)
+        f, g = lat.populations()
+        lat.close()
+        assert np.isfinite(f).all() and np.isfinite(g).all()
+        if ref is None:
+            ref = (f, g)
+        else:
+            assert np.array_equal(f, ref[0]) and np.array_equal(g, ref[1]), (by, zc)
+
+
+def test_chunk_choice_and_occupancy(lblib, cuda):
+    """The default launch of the FP32 and 16-bit forms keeps two CTAs of 256 threads per SM with
+    at most 128 registers a thread, and picks the chunk count that minimises the wave cost
+    ceil(CTAs / slots) * (zc + 4) over zc = 8..128."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for prec in (lb.LB_FP32, lb.LB_FP16_DEV):
+        for n in (64, 128):
+            w = config.single_phase_cell(n, precision=prec)
+            rho, T = w.fields()
+            lat = lb.Lattice(w.params, rho, T)
+            info = lat.launch_info()
+            lat.close()
+            assert info["threads_per_cta"] == 256 and info["ctas_per_sm"] == 2
+            assert info["registers"] <= 128
+            ntiles = (n // 32) * (n // 8)
+            assert info["grid"][0] == ntiles
+            slots = 2 * sms
+            costs = {}
+            for nch in range(1, n + 1):
+                zc = -(-n // nch)
+                if zc > 128:
+                    continue
+                if zc < 8 and nch > 1:
+                    break
+                ctas = ntiles * -(-n // zc)
+                costs.setdefault(zc, -(-ctas // slots) * (zc + 4))
+            best = min(costs.values())
+            zc_used = -(-n // info["grid"][1])
+            assert costs[zc_used] == best, (n, info, costs)
