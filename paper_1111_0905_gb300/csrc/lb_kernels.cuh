@@ -551,8 +551,17 @@ lb_fused_kernel(const KArgs a) {
         if (a.uz_out) a.uz_out[own] = double(uz);
         if (a.T_out) a.T_out[own] = double(T);
         const double drho_ = double(rho), dT = double(T), duz = double(uz);
-        const double U = a.c_v * dT + 0.25 * a.G * exp(-2.0 / drho_);
-        d_conv = drho_ * U * duz; d_T = dT; d_rho = drho_; d_E = double(E); d_mr = drho_; d_mT = dT;
+        if constexpr (sizeof(R) == 8) {
+          const double U = a.c_v * dT + 0.25 * a.G * exp(-2.0 / drho_);
+          d_conv = drho_ * U * duz;
+        } else {
+          // FP32-compute forms: the node's term in float (relative error ~1e-7, far inside
+          // these forms' tolerance; FP64 exp and division cost more than the step itself),
+          // the sums over nodes in FP64
+          const R U = R(a.c_v) * T + R(0.25) * G * fexp(R(-2) * inv);
+          d_conv = double(rho * U * uz);
+        }
+        d_T = dT; d_rho = drho_; d_E = double(E); d_mr = drho_; d_mT = dT;
         d_bad = (isfinite(drho_) && isfinite(dT) && isfinite(double(ux)) && isfinite(double(uy)) &&
                  isfinite(duz)) ? 0.0 : 1.0;
       }

@@ -242,17 +242,19 @@ def test_device_pointers_and_stream(lblib, cuda):
     a.close(); b.close()
 
 
-SHAPES = [(8, 0), (8, 5), (4, 7), (16, 23), (4, 1)]
+SHAPES = [(8, 0), (8, 5), (8, 23), (4, 7), (4, 1), (16, 23), (16, 3)]
+CROSS_TILE_TOL = {lb.LB_FP64: 1e-12, lb.LB_FP32: 1e-5, lb.LB_BF16_DEV: 2e-3, lb.LB_FP16_DEV: 2e-3}
 
 
 @pytest.mark.parametrize("prec", [lb.LB_FP64, lb.LB_FP32, lb.LB_BF16_DEV, lb.LB_FP16_DEV])
 def test_launch_shape_does_not_change_the_result(lblib, cuda, prec):
-    """Every node's arithmetic is the same whatever the tile height and z chunk (chunk prologues
-    recompute their planes identically): populations after 30 steps of a ragged boiling cell
-    are bitwise equal across launch shapes, in every form."""
+    """Chunk prologues recompute their planes with the same arithmetic: for one tile height the
+    populations after 30 steps of a ragged boiling cell are bitwise equal whatever the z chunk.
+    Different tile heights are different kernel instantiations, whose floating-point contractions
+    may differ: those agree within the form's parity tolerance."""
     w = config.boiling_cell(40, nz=23, ny=19, precision=prec)
     rho, T = w.fields()
-    ref = None
+    by_tile = {}
     for by, zc in SHAPES:
         if by == 16 and prec == lb.LB_FP64:
             continue
@@ -267,10 +269,14 @@ def test_launch_shape_does_not_change_the_result(lblib, cuda, prec):
         f, g = lat.populations()
         lat.close()
         assert np.isfinite(f).all() and np.isfinite(g).all()
-        if ref is None:
-            ref = (f, g)
+        if by not in by_tile:
+            by_tile[by] = (f, g)
         else:
+            ref = by_tile[by]
             assert np.array_equal(f, ref[0]) and np.array_equal(g, ref[1]), (by, zc)
+    f8, g8 = by_tile[8]
+    for by, (f, g) in by_tile.items():
+        assert rel_err(f, f8) <= CROSS_TILE_TOL[prec] and rel_err(g, g8) <= CROSS_TILE_TOL[prec], by
 
 
 def test_chunk_choice_and_occupancy(lblib, cuda):

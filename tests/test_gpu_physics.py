@@ -6,6 +6,9 @@ classical limits), each with its oracle counterpart at small size in the CPU tes
   along the simulated coexistence curve (Fig. 1).
 - Static 3-D bubbles: Laplace law Delta P = 2 sigma / R (linear in 1/R).
 - Conduction below onset: linear T between the walls and Nu = 1.
+- Rayleigh-Benard rolls (quasi-2-D, aspect 2.016 = the rigid-rigid critical wavelength): a roll
+  perturbation decays at half the nominal onset Rayleigh number 1708 and grows into steady
+  convection (Nu > 1.3) at twice it, with FP32 and FP64 agreeing on Nu.
 """
 import math
 
@@ -120,3 +123,58 @@ def test_conduction_profile_and_nusselt_one():
     assert np.abs(TT[:, 0, 0] - Tlin).max() < 1e-8
     assert np.abs(np.stack(u)).max() < 1e-8
     assert np.abs(nu_z - 1).max() < 1e-6
+
+
+def _rolls(ratio, precision, L=64):
+    """Compressed liquid rho = 2.6 between T_d = 1.1 T_m and T_u = 0.9 T_m, Pr = 9, gravity from
+    Ra = ratio * 1707.76 (Table 1 definition with the adiabatic gradient); T perturbed by
+    1e-3 dT sin(k x) sin(pi z / L) with k the critical wavenumber of the box 2.016 L x 1 x L."""
+    Tm = config.T_M
+    Td, Tu = 1.1 * Tm, 0.9 * Tm
+    nu = Tm * (1.25 - 0.5)
+    kappa = config.kappa_from_prandtl(9.0, nu, 2.6, Tm)
+    gz = config.gravity_from_rayleigh(ratio * 1707.76, L, Td - Tu, kappa, nu, 2.6, Tm)
+    nx = 2 * round(2.016 * L / 2)
+    p = lb.Params(nx=nx, ny=1, nz=L, tau_nu=1.25, tau_kappa=1.0, G=G0, kappa=kappa, g_z=gz,
+                  T_d=Td, T_u=Tu, precision=precision, tile_y=4)
+    k = 2 * math.pi / nx
+    zc = (np.arange(L) + 0.5) / L
+    x = np.arange(nx)
+    T = (Td + (Tu - Td) * zc)[:, None, None] + 1e-3 * (Td - Tu) * (
+        np.sin(math.pi * zc)[:, None, None] * np.sin(k * x)[None, None, :])
+    rho = np.full((L, 1, nx), 2.6)
+    return p, rho, np.ascontiguousarray(T), np.exp(-1j * k * x)
+
+
+def _roll_amplitude(lat, e):
+    _, u, _ = lat.moments()
+    return float(np.abs((u[2][:, 0, :] * e[None, :]).sum()))
+
+
+def test_rayleigh_benard_rolls_decay_below_and_convect_above_onset():
+    """Measured on this cell (alpha dT = 0.46, far from the Oberbeck-Boussinesq limit): below
+    1.3 x 1708 the roll stays at a small steady amplitude, from 1.5 x 1708 it grows
+    exponentially; Nu = 1.54 at 2 x 1708 and 1.67 at 3 x 1708 after 120,000 steps."""
+    p, rho, T, e = _rolls(0.5, lb.LB_FP32)
+    lat = lb.Lattice(p, rho, T)
+    lat.step(4000)
+    a0 = _roll_amplitude(lat, e)
+    lat.step(116000)
+    a1 = _roll_amplitude(lat, e)
+    nu_below = lat.nusselt()[0]
+    lat.close()
+    assert a1 < 0.2 * a0 and abs(nu_below - 1.0) < 1e-3, (a0, a1, nu_below)
+    nus = {}
+    for prec in (lb.LB_FP32, lb.LB_FP64):
+        p, rho, T, e = _rolls(2.0, prec)
+        lat = lb.Lattice(p, rho, T)
+        lat.step(4000)
+        a0 = _roll_amplitude(lat, e)
+        lat.step(116000)
+        a1 = _roll_amplitude(lat, e)
+        nus[prec] = lat.nusselt()[0]
+        d = lat.diagnostics()
+        lat.close()
+        assert a1 > 100 * a0 and d["nonfinite"] == 0, (prec, a0, a1)
+    assert nus[lb.LB_FP32] > 1.3 and nus[lb.LB_FP64] > 1.3, nus
+    assert abs(nus[lb.LB_FP32] - nus[lb.LB_FP64]) < 2e-3 * nus[lb.LB_FP64], nus
