@@ -86,3 +86,72 @@ def rayleigh(g, rho, T, G, L, dT, kappa, nu, c_v=1.0):
     cp = c_p(rho, T, G, c_v)
     chi = kappa / (rho * cp)
     return g * b * L ** 4 * (dT / L - b * T * g / cp) / (chi * nu)
+
+
+# ---------------------------------------------------------------------------------------
+# Van der Waals-type pseudopotential variant (a comparison, not the paper's psi):
+# psi^2 = 2 (P_vdW(rho, T_v) - rho T_v) / G, so the bulk pressure of the lattice fluid is
+# P = rho T + rho^2 (b T_v / (1 - b rho) - a): at T = T_v exactly the van der Waals pressure
+# rho T/(1 - b rho) - a rho^2, whose critical point is rho_c = 1/(3b), T_c = 8a/(27b).
+# ---------------------------------------------------------------------------------------
+
+def pressure_vdw(rho, T, a, b, Tv):
+    """P(rho, T) = rho T + rho^2 (b T_v/(1 - b rho) - a)."""
+    return rho * T + rho * rho * (b * Tv / (1.0 - b * rho) - a)
+
+
+def dP_drho_vdw(rho, T, a, b, Tv):
+    """(dP/drho)_T = T + 2 rho b T_v/(1 - b rho) + rho^2 b^2 T_v/(1 - b rho)^2 - 2 a rho."""
+    x = 1.0 - b * rho
+    return T + 2.0 * rho * b * Tv / x + rho * rho * b * b * Tv / (x * x) - 2.0 * a * rho
+
+
+def chemical_potential_vdw(rho, T, a, b, Tv):
+    """mu with dmu = dP/rho at fixed T: T ln rho - T_v ln(1 - b rho) + T_v/(1 - b rho) - 2 a rho."""
+    x = 1.0 - b * rho
+    return T * np.log(rho) - Tv * np.log(x) + Tv / x - 2.0 * a * rho
+
+
+def critical_point_vdw(a, b):
+    """(rho_c, T_c, P_c) = (1/(3b), 8a/(27b), a/(27 b^2)) of the van der Waals pressure (T = T_v)."""
+    return 1.0 / (3.0 * b), 8.0 * a / (27.0 * b), a / (27.0 * b * b)
+
+
+def coexistence_vdw(T, a, b, Tv):
+    """Maxwell construction of pressure_vdw at temperature T: (rho_g, rho_l)."""
+    rc = 1.0 / (3.0 * b)
+    f = lambda r: dP_drho_vdw(r, T, a, b, Tv)
+    s_lo = brentq(f, 1e-6 * rc, rc)
+    s_hi = brentq(f, rc, 0.999 / b)
+
+    def eqs(x):
+        rg, rl = x
+        return [pressure_vdw(rg, T, a, b, Tv) - pressure_vdw(rl, T, a, b, Tv),
+                chemical_potential_vdw(rg, T, a, b, Tv) - chemical_potential_vdw(rl, T, a, b, Tv)]
+
+    rg, rl = fsolve(eqs, [0.5 * s_lo, min(1.3 * s_hi, 0.5 * (s_hi + 1.0 / b))], xtol=1e-12)
+    if not (rg < s_lo < s_hi < rl):
+        raise ValueError("Maxwell construction did not converge to a two-phase solution")
+    return float(rg), float(rl)
+
+
+def coexistence_psi_rule(P, psi, dpsi, s_lo, s_hi, eps, guess):
+    """Flat-interface coexistence of a pseudopotential fluid with bulk pressure P(rho) and
+    pseudopotential psi(rho): P(rho_g) = P(rho_l) = P0 and
+    int_{rho_g}^{rho_l} (P0 - P(rho)) psi'(rho)/psi(rho)^(1+eps) drho = 0.
+    eps = 0 is the equal-area rule in ln(psi) (Maxwell's rule when psi = exp(-c/rho));
+    eps = 1 is the equal-area rule in 1/psi, the mechanical balance T rho' = -G psi (psi' +
+    psi'''/6) of the Eq. (9) force expanded to third derivatives with an isotropic ideal part."""
+    from scipy.integrate import quad
+
+    def eqs(x):
+        rg, rl = x
+        P0 = P(rg)
+        integ = quad(lambda r: (P0 - P(r)) * dpsi(r) / psi(r) ** (1.0 + eps), rg, rl,
+                     epsabs=1e-14, epsrel=1e-12, limit=200)[0]
+        return [P(rl) - P0, integ]
+
+    rg, rl = fsolve(eqs, guess, xtol=1e-12)
+    if not (rg < s_lo < s_hi < rl):
+        raise ValueError("psi-rule construction did not converge to a two-phase solution")
+    return float(rg), float(rl)

@@ -29,6 +29,12 @@ Readings (the paper leaves these open):
     the wall temperature and the density of the wall node at the colliding step.
   * Gravity: full-rho body force rho*g_z*z_hat added to F.
 
+Variants for comparison (Params.forcing, Params.psi_kind; the paper's scheme is the default):
+  * Guo forcing: f^eq at the physical velocity u plus (1 - 1/(2 tau_nu)) S_l with
+    S_l = w_l [3 (c_l - u).F + 9 (c_l.u)(c_l.F)] (Guo, Zheng, Shi, Phys. Rev. E 65, 046308).
+  * Van der Waals-type pseudopotential psi = sqrt(2 rho^2 (b T_v/(1 - b rho) - a)/G): the bulk
+    pressure is rho T + the non-ideal van der Waals pressure at the temperature T_v.
+
 State convention: the state at time n is the pre-collision (post-streaming) pair (f, g),
 each a tensor [19, nz, ny, nx] (x fastest). All arithmetic is float64, sums over l in
 ascending order.
@@ -73,6 +79,14 @@ class Params:
     T_d: float = 1.0 / 3.0  # bottom wall temperature
     T_u: float = 1.0 / 3.0  # top wall temperature
     periodic_z: bool = False  # test-only: replace the walls by periodic z
+    # Variants (comparisons, not the paper's scheme): forcing "shift" (the paper's velocity
+    # shift) or "guo" (tau-independent source term); pseudopotential "exp" (the paper's
+    # exp(-1/rho)) or "vdw" (van der Waals attraction and excluded volume at temperature vdw_T).
+    forcing: str = "shift"
+    psi_kind: str = "exp"
+    vdw_a: float = 5.0 / 42.0
+    vdw_b: float = 2.0 / 21.0
+    vdw_T: float = 1.0 / 3.0
 
     @property
     def lam(self) -> float:
@@ -186,9 +200,23 @@ def force_weight(l: int) -> float:
     return {1: 1.0 / 6.0, 2: 1.0 / 12.0}[C2[l]]
 
 
+def psi_vdw(rho, p: Params):
+    """Pseudopotential whose bulk pressure rho T + (G/2) psi^2 has the non-ideal part of the van
+    der Waals pressure at temperature T_v, rho T_v/(1 - b rho) - a rho^2 - rho T_v:
+    psi = sqrt(2 rho^2 (b T_v/(1 - b rho) - a) / G) (G < 0; real for b T_v < a (1 - b rho))."""
+    return torch.sqrt(2.0 * rho * rho * (p.vdw_b * p.vdw_T / (1.0 - p.vdw_b * rho) - p.vdw_a) / p.G)
+
+
+def psi_of(rho, p: Params):
+    """The pseudopotential of the run: exp(-1/rho) (the paper) or the van der Waals variant."""
+    if p.psi_kind == "vdw":
+        return psi_vdw(rho, p)
+    return psi(rho)
+
+
 def force(rho, p: Params):
     """F = -G psi(x) sum_{l=1..18} W_l c_l psi(x + c_l) + rho g_z z_hat."""
-    ps = psi(rho)
+    ps = psi_of(rho, p)
     acc = [torch.zeros_like(rho) for _ in range(3)]
     for l in range(1, Q):
         nb = shifted(ps, C[l][0], C[l][1], C[l][2], p)
@@ -220,8 +248,9 @@ def macroscopic(f, g, p: Params):
     rho, j = density_momentum(f)
     T = energy(g) / rho
     F = force(rho, p)
-    u_eq = (j + p.tau_nu * F) / rho
     u = (j + 0.5 * F) / rho
+    # velocity shift (the paper): f^eq at u' = (j + tau F)/rho; Guo forcing: f^eq at u
+    u_eq = u if p.forcing == "guo" else (j + p.tau_nu * F) / rho
     return rho, j, T, F, u_eq, u
 
 
@@ -230,11 +259,27 @@ def macroscopic(f, g, p: Params):
 # sides) with the wall rules.
 # ---------------------------------------------------------------------------------------
 
+def guo_source(u, F):
+    """S_l = w_l [3 (c_l - u).F + 9 (c_l.u)(c_l.F)] (Guo, Zheng, Shi 2002, with c_s^2 = 1/3).
+
+    Moments: sum = 0, sum c = F, sum c c = u F + F u.
+    """
+    uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2]
+    out = []
+    for l in range(Q):
+        cu = C[l][0] * u[0] + C[l][1] * u[1] + C[l][2] * u[2]
+        cF = C[l][0] * F[0] + C[l][1] * F[1] + C[l][2] * F[2]
+        out.append(W[l] * (3.0 * (cF - uF) + 9.0 * cu * cF))
+    return torch.stack(out)
+
+
 def collide(f, g, p: Params):
     """Post-collision f*, g* and the density used by the thermal wall rule."""
     rho, j, T, F, u_eq, u = macroscopic(f, g, p)
     feq = equilibrium_f(rho, u_eq, T)
     fstar = f - (f - feq) / p.tau_nu
+    if p.forcing == "guo":
+        fstar = fstar + (1.0 - 0.5 / p.tau_nu) * guo_source(u, F)
     D = divergence(u, p)
     S = -rho * T * D / p.c_v
     geq = equilibrium_g(rho, T, u, p.lam)
@@ -300,7 +345,10 @@ def run(f, g, p: Params, nsteps: int):
 # ---------------------------------------------------------------------------------------
 
 def internal_energy(rho, T, p: Params):
-    """U = c_v T + int drho P_NI/rho^2 = c_v T + (G/4) exp(-2/rho) (Eq. (2), zero at rho -> 0)."""
+    """U = c_v T + int_0^rho P_NI(s)/s^2 ds (Eq. (2), zero at rho -> 0): (G/4) exp(-2/rho) for
+    the paper's psi; -T_v ln(1 - b rho) - a rho for the van der Waals variant."""
+    if p.psi_kind == "vdw":
+        return p.c_v * T - p.vdw_T * torch.log(1.0 - p.vdw_b * rho) - p.vdw_a * rho
     return p.c_v * T + 0.25 * p.G * torch.exp(-2.0 / rho)
 
 
