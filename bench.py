@@ -289,6 +289,7 @@ def run_ours(args):
 
     # the sizes the HBM target is stated at (256^3, 512^3), same kernel, paper-geometry boiling cell
     sizes = {} if args.no_sizes else size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws)
+    variants = {} if args.no_sizes else variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws)
 
     main = results[main_form]
     src_hash = kernel_src_hash()
@@ -311,7 +312,7 @@ def run_ours(args):
                "data": "synthetic (seeded SplitMix64 fields; no dataset)",
                "config": config_dict(w, main_form), "roofline": roofline, "cpu_baseline": cpu,
                "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_summary,
-               "forms": results, "sizes": sizes, "kernel_src_hash": src_hash}
+               "forms": results, "sizes": sizes, "variants": variants, "kernel_src_hash": src_hash}
         print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
@@ -349,6 +350,43 @@ def size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
             out[f"{n}^3_{form}"] = {"glups": N / (ms * 1e-3) / 1e9 * ws, "ms_per_step": ms,
                                     "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                     "workload": w.name, "launch": launch}
+    return out
+
+
+def variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
+    """GLUPS of the scheme variants (Guo forcing, van der Waals psi) in the FP32 form on the 128^3
+    single-phase cell (the van der Waals psi with its liquid, rho = 6.0 at T_m; a = 5/42,
+    b = 2/21), 200 timed steps after 10 warm-up steps each, beside the paper's scheme."""
+    from paper_1111_0905_gb300 import config, synthetic
+    out = {}
+    for name, forcing, psi in (("paper", 0, 0), ("guo", 1, 0), ("vdw", 0, 1), ("guo+vdw", 1, 1)):
+        w = config.single_phase_cell(128, precision=FORMS["f32"])
+        p = w.params
+        p.forcing, p.psi_kind = forcing, psi
+        rho, T = w.fields()
+        if psi:
+            p.G = -1.0
+            rho, T = synthetic.single_phase_fields(p.nx, p.ny, p.nz, 6.0, p.T_d, p.T_u)
+        N = p.nx * p.ny * p.nz
+        lat = lb.Lattice(p, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+        launch = lat.launch_info()
+        lat.step(10)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        K = 200
+        e0.record()
+        lat.step(K)
+        e1.record()
+        e1.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1)) / K
+        health = lat.diagnostics()
+        lat.close()
+        bytes_step = 4 * Q * STORE_BYTES["f32"] * N
+        out[name] = {"glups": N / (ms * 1e-3) / 1e9 * ws, "ms_per_step": ms,
+                     "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                     "registers": launch["registers"], "nonfinite": int(health["nonfinite"])}
     return out
 
 

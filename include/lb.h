@@ -52,6 +52,18 @@ typedef enum {
 /* Every precision stores deviations from the reference equilibria, f_l - f^eq_l(rho0, 0, T0) and
  * g_l - g^eq_l(rho0, T0, 0), and forms moments and equilibria from them. */
 
+/* Scheme variants for comparison with the paper's scheme (variant 0 of each; the paper defines
+ * neither alternative). Forcing: LB_FORCE_SHIFT, the paper's equilibrium velocity
+ * u' = (j + tau_nu F)/rho; LB_FORCE_GUO, f^eq at the physical velocity u = (j + F/2)/rho plus
+ * (1 - 1/(2 tau_nu)) w_l [3 (c_l - u).F + 9 (c_l.u)(c_l.F)] (Guo, Zheng, Shi, PRE 65, 046308).
+ * Pseudopotential: LB_PSI_EXP, psi = exp(-1/rho) of the "Algorithm" paragraph; LB_PSI_VDW,
+ * psi = rho sqrt(2 (a - b T_v/(1 - b rho))/(-G)) (G < 0), whose bulk pressure
+ * rho T + (G/2) psi^2 carries the non-ideal van der Waals pressure at temperature T_v. */
+#define LB_FORCE_SHIFT 0
+#define LB_FORCE_GUO 1
+#define LB_PSI_EXP 0
+#define LB_PSI_VDW 1
+
 typedef struct {
   int nx, ny, nz;         /* grid; each >= 1, 19*nx*ny*nz < 2^32 */
   double tau_nu;          /* f relaxation time, Eq. (6); > 1/2 */
@@ -66,8 +78,13 @@ typedef struct {
   int nu_every;           /* > 0: accumulate Nu_mean every nu_every steps into the time average */
   int check_every;        /* > 0: lb_step checks rho > 0, T > 0, no NaN every check_every steps */
   int tile_y;             /* launch shape: CTA tile is 32 x tile_y (4, 8 or 16; 16 not with FP64;
-                             0 = default: 16 for FP32, 8 otherwise) */
+                             0 = default: 8) */
   int z_chunk;            /* launch shape: planes per CTA (0 = choose from the grid size) */
+  int forcing;            /* LB_FORCE_SHIFT (0, the paper) or LB_FORCE_GUO */
+  int psi_kind;           /* LB_PSI_EXP (0, the paper) or LB_PSI_VDW */
+  double vdw_a, vdw_b;    /* LB_PSI_VDW: attraction a > 0 and excluded volume b > 0 */
+  double vdw_T;           /* LB_PSI_VDW: temperature T_v > 0 of the non-ideal pressure; b T_v < a
+                             (1 - b rho) must hold for every density the run reaches */
 } lb_params;
 
 typedef struct lb_ctx lb_ctx;  /* opaque */
@@ -77,18 +94,21 @@ typedef struct lb_ctx lb_ctx;  /* opaque */
  * rho_init, T_init: float64 fields (node-index order), host memory if init_on_device == 0,
  * device memory otherwise; copied, not retained. cuda_stream: a cudaStream_t (NULL = the
  * legacy default stream) on the current device; every later call is ordered on it.
- * On success *out is the new context. Errors: LB_EINVAL (parameters, rho <= 0 or T <= 0 or
+ * On success *out is the new context. Errors: LB_EINVAL (parameters, an unknown variant, a
+ * van der Waals psi that is not real at some initial density, rho <= 0 or T <= 0 or
  * non-finite input), LB_ENOMEM, LB_ECUDA. On error *out is NULL and nothing is leaked. */
 int lb_init(const lb_params* params, const double* rho_init, const double* T_init,
             int init_on_device, void* cuda_stream, lb_ctx** out);
 
 /* lb_step -- advance nsteps time steps of Eqs. (6)-(7): per step one fused launch that pull-
  * streams f and g (periodic x/y, bounce-back walls), takes the moments of Eq. (8), the force of
- * Eq. (9) with psi = exp(-1/rho) plus gravity rho g_z z, the shifted velocity u' = (j + tau_nu F)/rho,
+ * Eq. (9) with psi = exp(-1/rho) plus gravity rho g_z z (psi_kind selects the variant), the shifted
+ * velocity u' = (j + tau_nu F)/rho (forcing selects the variant),
  * the physical velocity u = (j + F/2)/rho and its divergence, and collides f (temperature in
  * f^eq) and g (with the counter term -rho T div u / c_v). Asynchronous on the context's stream
  * unless nu_every/check_every ask for host-visible checks. nsteps >= 0.
- * Errors: LB_EINVAL, LB_ECUDA (launch), LB_ENONPHYS (health check failed; the state is kept). */
+ * Errors: LB_EINVAL, LB_ECUDA (launch), LB_ENONPHYS (health check failed, e.g. a density beyond
+ * the range where the van der Waals psi is real; the state is kept). */
 int lb_step(lb_ctx* ctx, long long nsteps);
 
 /* lb_moments -- macroscopic fields of the current state (Eq. (8)): rho, the physical velocity
@@ -118,7 +138,8 @@ int lb_nusselt(lb_ctx* ctx, double* nu_mean, double* nu_z, double* nu_time_avg);
  * Device memory: nsteps/checkpoint_every + 1 population checkpoints, checkpoint_every + 1 float64
  * states, 2 float64 adjoint states and ~35 float64 fields, allocated and freed by the call.
  * Synchronises. Errors: LB_EINVAL (nsteps < 1, checkpoint_every < 1, T_d == T_u, dJ_dT0 requested
- * after lb_step), LB_ENOMEM, LB_ECUDA. */
+ * after lb_step), LB_EUNSUP (a scheme variant: the reverse pass transposes the paper's scheme
+ * only), LB_ENOMEM, LB_ECUDA. */
 int lb_adjoint_step(lb_ctx* ctx, long long nsteps, int checkpoint_every, double* J,
                     double* dJ_dTd, double* dJ_dTu, double* dJ_dG, double* dJ_dT0);
 

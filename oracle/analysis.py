@@ -15,10 +15,14 @@ from . import lbm
 
 
 def profiles(f, g, p: lbm.Params):
-    """Per-plane means of rho, T and P div(u), P = rho T + (G/2) e^{-2/rho} (bulk pressure)."""
+    """Per-plane means of rho, T and P div(u), P = rho T + (G/2) psi^2 (bulk pressure: with the
+    paper's psi (G/2) e^{-2/rho}, with the van der Waals psi rho^2 (b T_v/(1 - b rho) - a))."""
     rho, u, T = lbm.moments_out(f, g, p)
     D = lbm.divergence(u, p)
-    P = rho * T + 0.5 * p.G * torch.exp(-2.0 / rho)
+    if p.psi_kind == "vdw":
+        P = rho * T + rho * rho * (p.vdw_b * p.vdw_T / (1.0 - p.vdw_b * rho) - p.vdw_a)
+    else:
+        P = rho * T + 0.5 * p.G * torch.exp(-2.0 / rho)
     return rho.mean(dim=(1, 2)), T.mean(dim=(1, 2)), (P * D).mean(dim=(1, 2))
 
 

@@ -26,11 +26,13 @@ __device__ double block_sum(double v, double* sh) {
   return s;
 }
 
-// One block per plane z: sums of rho, T and P div(u), P = rho T + (G/2) e^{-2/rho}, div(u) by
-// central differences with u_z -> -u_z across the walls (the step's divergence).
+// One block per plane z: sums of rho, T and P div(u), P = rho T + (G/2) e^{-2/rho} (or, for
+// the van der Waals psi, rho T + rho^2 (b T_v/(1 - b rho) - a)), div(u) by central differences
+// with u_z -> -u_z across the walls (the step's divergence).
 __global__ void profiles_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
                                 const double* __restrict__ uy, const double* __restrict__ uz,
                                 const double* __restrict__ T, int nx, int ny, int nz, double G,
+                                int psi_kind, double va, double vb, double vT,
                                 double* __restrict__ out /* [nz][3] */) {
   __shared__ double sh[32];
   const int z = blockIdx.x;
@@ -46,7 +48,8 @@ __global__ void profiles_kernel(const double* __restrict__ rho, const double* __
     const double D = 0.5 * (ux[base + y * nx + (x + 1) % nx] - ux[base + y * nx + (x + nx - 1) % nx]) +
                      0.5 * (uy[base + ((y + 1) % ny) * nx + x] - uy[base + ((y + ny - 1) % ny) * nx + x]) +
                      0.5 * (uzp - uzm);
-    const double P = r * t + 0.5 * G * exp(-2.0 / r);
+    const double P = r * t + ((psi_kind == PSI_VDW) ? r * r * (vb * vT / (1.0 - vb * r) - va)
+                                                    : 0.5 * G * exp(-2.0 / r));
     sr += r; sT += t; sPD += P * D;
   }
   const double a = block_sum(sr, sh), b = block_sum(sT, sh), c = block_sum(sPD, sh);
@@ -143,6 +146,7 @@ extern "C" int lb_profiles(lb_ctx* c, double* rho_z, double* T_z, double* PdivU_
   DevBuf out;
   if (cudaMalloc(&out.p, (size_t)3 * nz * sizeof(double)) != cudaSuccess) return lb_fail(c, LB_ENOMEM, "profiles");
   ana::profiles_kernel<<<nz, 256, 0, c->stream>>>(rho, ux, uy, uz, T, c->p.nx, c->p.ny, nz, c->p.G,
+                                                  c->p.psi_kind, c->p.vdw_a, c->p.vdw_b, c->p.vdw_T,
                                                   static_cast<double*>(out.p));
   LB_CU(c, cudaGetLastError());
   std::vector<double> h((size_t)3 * nz);

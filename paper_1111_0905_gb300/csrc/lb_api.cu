@@ -82,12 +82,12 @@ __global__ void __launch_bounds__(1024) lb_diag_finalize(const double* __restric
 
 // Validation of initial fields: per-block count of bad entries and sums (fixed order).
 __global__ void lb_validate_kernel(const double* __restrict__ rho, const double* __restrict__ T,
-                                   int N, double* __restrict__ out /* [gridDim.x][3] */) {
+                                   int N, double rho_lim, double* __restrict__ out /* [gridDim.x][3] */) {
   __shared__ double sh[3][256];
   double bad = 0.0, sr = 0.0, sT = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double r = rho[i], t = T[i];
-    if (!(r > 0.0) || !(t > 0.0) || !isfinite(r) || !isfinite(t)) bad += 1.0;
+    if (!(r > 0.0) || !(r < rho_lim) || !(t > 0.0) || !isfinite(r) || !isfinite(t)) bad += 1.0;
     sr += r; sT += t;
   }
   sh[0][threadIdx.x] = bad; sh[1][threadIdx.x] = sr; sh[2][threadIdx.x] = sT;
@@ -129,15 +129,17 @@ KArgs make_args(const lb_ctx* c) {
   a.fout = c->f[1 - c->cur]; a.gout = c->g[1 - c->cur];
   a.nx = c->p.nx; a.ny = c->p.ny; a.nz = c->p.nz; a.plane = c->plane; a.N = c->N;
   a.tiles_x = c->tiles_x; a.ntiles = c->ntiles; a.zc = c->zc;
+  a.forcing = c->p.forcing; a.psi_kind = c->p.psi_kind;
   a.tau_nu = c->p.tau_nu; a.omega_nu = 1.0 / c->p.tau_nu; a.omega_kappa = 1.0 / c->p.tau_kappa;
   a.G = c->p.G; a.g_z = c->p.g_z; a.lam = c->lam; a.inv_cv = 1.0 / c->p.c_v; a.c_v = c->p.c_v;
   a.kappa = c->p.kappa; a.T_d = c->p.T_d; a.T_u = c->p.T_u;
   a.rho0 = c->rho0; a.T0 = c->T0; a.E0 = c->rho0 * c->T0;
+  const double vk = c->p.psi_kind == PSI_VDW ? 2.0 / (-c->p.G) : 0.0;
   a.pd = {a.tau_nu, a.omega_nu, a.omega_kappa, a.G, a.g_z, a.lam, a.inv_cv, a.T_d, a.T_u,
-          a.rho0, a.T0, a.E0};
+          a.rho0, a.T0, a.E0, c->p.vdw_a, c->p.vdw_b, c->p.vdw_T, vk};
   a.pf = {(float)a.tau_nu, (float)a.omega_nu, (float)a.omega_kappa, (float)a.G, (float)a.g_z,
           (float)a.lam, (float)a.inv_cv, (float)a.T_d, (float)a.T_u, (float)a.rho0, (float)a.T0,
-          (float)a.E0};
+          (float)a.E0, (float)c->p.vdw_a, (float)c->p.vdw_b, (float)c->p.vdw_T, (float)vk};
   // reference equilibria per class (rest, axis, diagonal): f^eq(rho0, 0, T0), g^eq(rho0, T0, 0)
   const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
   for (int k = 0; k < 3; ++k) {
@@ -217,7 +219,7 @@ long long lb_step_count(const lb_ctx* c) { return c ? c->step : -1; }
 int lb_launch_info(lb_ctx* c, int* out) {
   if (!c || !out) return LB_EINVAL;
   int k[4] = {0, 0, 0, 0};
-  LB_CU(c, c->ops->info(c->by, k));
+  LB_CU(c, c->ops->info(c->by, variant_of(c->p.forcing, c->p.psi_kind), k));
   const dim3 grid = fused_grid(c);
   out[0] = (int)grid.x; out[1] = (int)grid.y;
   out[2] = k[0]; out[3] = k[1]; out[4] = k[2]; out[5] = k[3];
@@ -243,6 +245,16 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   if (!ops->tile_ok(by)) return LB_EINVAL;
   if ((long long)Q * N >= (1ll << 32)) return LB_EINVAL;   // 32-bit population offsets
   if (p.z_chunk < 0 || p.nu_every < 0 || p.check_every < 0) return LB_EINVAL;
+  if (p.forcing != FORCE_SHIFT && p.forcing != FORCE_GUO) return LB_EINVAL;
+  if (p.psi_kind != PSI_EXP && p.psi_kind != PSI_VDW) return LB_EINVAL;
+  // van der Waals psi: real for rho < (1 - b T_v/a)/b; every initial density must be below it
+  double rho_lim = INFINITY;
+  if (p.psi_kind == PSI_VDW) {
+    if (!(p.G < 0.0) || !(p.vdw_a > 0.0) || !(p.vdw_b > 0.0) || !(p.vdw_T > 0.0) ||
+        !(p.vdw_b * p.vdw_T < p.vdw_a))
+      return LB_EINVAL;
+    rho_lim = (1.0 - p.vdw_b * p.vdw_T / p.vdw_a) / p.vdw_b;
+  }
 
   lb_ctx* c = new (std::nothrow) lb_ctx();
   if (!c) return LB_ENOMEM;
@@ -268,7 +280,7 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
     // ceil(CTAs / slots) * (zc + 4) plane-steps. Take the chunk count (zc from 8 to 128, or nz)
     // that minimises it; ties go to the larger chunk.
     int k[4] = {0, 0, 0, 0}, sms = 0;
-    if (ops->info(by, k) != cudaSuccess ||
+    if (ops->info(by, variant_of(p.forcing, p.psi_kind), k) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
       return bail(LB_ECUDA);
     const long long slots = (long long)(k[2] > 0 ? k[2] : 1) * (sms > 0 ? sms : 1);
@@ -303,7 +315,7 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   const int vblocks = 256;
   double* vpart = nullptr;
   if (cudaMalloc(&vpart, vblocks * 3 * sizeof(double)) != cudaSuccess) { cudaFree(staging); return bail(LB_ENOMEM); }
-  lb_validate_kernel<<<vblocks, 256, 0, c->stream>>>(d_rho, d_T, c->N, vpart);
+  lb_validate_kernel<<<vblocks, 256, 0, c->stream>>>(d_rho, d_T, c->N, rho_lim, vpart);
   std::vector<double> hv(vblocks * 3);
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(hv.data(), vpart, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -455,8 +467,8 @@ int lb_save(lb_ctx* c, const char* path) {
   std::vector<unsigned char> buf(2 * pbytes);
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
-  std::memcpy(h.magic, "TLBMCKP1", 8);
-  h.version = 1; h.precision = c->p.precision;
+  std::memcpy(h.magic, "TLBMCKP2", 8);
+  h.version = 2; h.precision = c->p.precision;
   h.nx = c->p.nx; h.ny = c->p.ny; h.nz = c->p.nz;
   h.step = c->step; h.rho0 = c->rho0; h.T0 = c->T0; h.params = c->p;
   LB_CU(c, cudaMemcpyAsync(buf.data(), c->f[c->cur], pbytes, cudaMemcpyDeviceToHost, c->stream));
@@ -481,7 +493,7 @@ int lb_load(lb_ctx* c, const char* path) {
   bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
   std::fclose(fp);
   if (!ok) return lb_fail(c, LB_EIO, "short read");
-  if (std::memcmp(h.magic, "TLBMCKP1", 8) != 0 || h.version != 1) return lb_fail(c, LB_EIO, "bad magic/version");
+  if (std::memcmp(h.magic, "TLBMCKP2", 8) != 0 || h.version != 2) return lb_fail(c, LB_EIO, "bad magic/version");
   if (h.nx != c->p.nx || h.ny != c->p.ny || h.nz != c->p.nz || h.precision != c->p.precision)
     return lb_fail(c, LB_EIO, "grid or precision mismatch");
   if (fnv1a(1469598103934665603ull, buf.data(), buf.size()) != h.checksum)

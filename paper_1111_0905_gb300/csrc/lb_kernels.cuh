@@ -91,13 +91,27 @@ template <> struct Store<__half> {
 // FP32 kernels never convert from double (conversions run on GB300's narrow FP64 pipe).
 template <class R> struct KPar {
   R tau_nu, omega_nu, omega_kappa, G, g_z, lam, inv_cv, T_d, T_u, rho0, T0, E0;
+  R va, vb, vT, vk;   // van der Waals-type psi: a, b, T_v, 2/(-G)
 };
+
+// Scheme variants (comparisons with the paper's scheme, which is variant 0 of each).
+constexpr int FORCE_SHIFT = 0;   // equilibrium velocity u' = (j + tau F)/rho (the paper)
+constexpr int FORCE_GUO = 1;     // f^eq at u = (j + F/2)/rho plus (1 - 1/(2 tau)) S_l
+constexpr int PSI_EXP = 0;       // psi = exp(-1/rho) (the paper)
+constexpr int PSI_VDW = 1;       // psi = rho sqrt(2 (a - b T_v/(1 - b rho))/(-G))
+// Kernel variant index: bit 0 = Guo forcing, bit 1 = van der Waals psi (0 = the paper's scheme;
+// a compile-time choice, so the paper's scheme carries no code of the variants).
+constexpr int VAR_GUO = 1, VAR_VDW = 2;
+__host__ __device__ constexpr int variant_of(int forcing, int psi_kind) {
+  return (forcing == FORCE_GUO ? VAR_GUO : 0) | (psi_kind == PSI_VDW ? VAR_VDW : 0);
+}
 
 struct KArgs {
   const void* fin; const void* gin;   // post-collision lattices of the previous step
   void* fout; void* gout;             // lattices written by this step
   int nx, ny, nz, plane, N;
   int tiles_x, ntiles, zc;
+  int forcing, psi_kind;              // FORCE_*, PSI_*
   double tau_nu, omega_nu, omega_kappa, G, g_z, lam, inv_cv, c_v, kappa, T_d, T_u;
   double rho0, T0, E0;                // reference state of the deviations (E0 = rho0 T0)
   double fbase[3], gbase[3];          // f^eq(rho0,0,T0), g^eq(rho0,T0,0) per class: rest, axis, diagonal
@@ -187,6 +201,14 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
+
+// van der Waals-type pseudopotential psi = rho sqrt(k (a - b T_v/(1 - b rho))), k = 2/(-G)
+__device__ __forceinline__ double psi_vdw(double rho, const KPar<double>& p) {
+  return rho * sqrt(p.vk * (p.va - p.vb * p.vT / (1.0 - p.vb * rho)));
+}
+__device__ __forceinline__ float psi_vdw(float rho, const KPar<float>& p) {
+  return rho * sqrtf(p.vk * (p.va - p.vb * p.vT / (1.0f - p.vb * rho)));
+}
 
 template <int BY> struct Geo {
   static constexpr int NT = BX * BY;
@@ -292,9 +314,11 @@ template <> __device__ __forceinline__ float cvt<__half, float>(__half v) { retu
 template <class S, int BY> struct MinBlocks { static constexpr int v = 512 / (BX * BY) > 0 ? 512 / (BX * BY) : 1; };
 template <int BY> struct MinBlocks<double, BY> { static constexpr int v = 1; };
 
-template <class S, int BY, int MODE>
+template <class S, int BY, int MODE, int VAR = 0>
 __global__ void __launch_bounds__(BX * BY, MinBlocks<S, BY>::v)
 lb_fused_kernel(const KArgs a) {
+  constexpr int FORCE = (VAR & VAR_GUO) ? FORCE_GUO : FORCE_SHIFT;
+  constexpr bool VDW = (VAR & VAR_VDW) != 0;
   using R = typename Store<S>::R;
   using GE = Geo<BY>;
   constexpr int NT = GE::NT, RX = GE::RX, RXY = GE::RXY, HX = GE::HX, HXY = GE::HXY;
@@ -396,7 +420,8 @@ lb_fused_kernel(const KArgs a) {
           density_momentum<R>(f, drho, jx, jy, jz);
           const R rho = rho0 + drho;
           const R inv = rcp(rho);
-          psi_s[s3 * RXY + k] = fexp(-inv);
+          if constexpr (VDW) psi_s[s3 * RXY + k] = psi_vdw(rho, kp);
+          else psi_s[s3 * RXY + k] = fexp(-inv);
           if (mh[i] >= 0) {
             R* rj = rj_s + s3 * 5 * HXY + mh[i];
             rj[0] = rho; rj[HXY] = inv; rj[2 * HXY] = jx; rj[3 * HXY] = jy; rj[4 * HXY] = jz;
@@ -503,9 +528,15 @@ lb_fused_kernel(const KArgs a) {
         // f: BGK towards f^eq(rho, u', T), u' = (j + tau F)/rho. f^eq - fbase per class:
         // w [drho - 1.5 rho v.v + 4.5 (|c|^2-1)(dE - drho/3) + 3 rho c.v + 4.5 rho (c.v)^2]
         // (rho (T - 1/3) - rho0 (T0 - 1/3) = dE - drho/3 since rho T = E).
+        // Guo forcing (variant): v = u and the source (1 - om/2) w [3 (c - u).F + 9 (c.u)(c.F)],
+        // split like f^eq into the part even in c (9 (c.u)(c.F) - 3 u.F) and the odd part 3 c.F.
         {
           const R tau = kp.tau_nu, om = kp.omega_nu, om1 = R(1) - om;
-          const R vx = (jx + tau * Fx) * inv, vy = (jy + tau * Fy) * inv, vz = (jz + tau * Fz) * inv;
+          const R vx = (FORCE == FORCE_GUO) ? ux : (jx + tau * Fx) * inv;
+          const R vy = (FORCE == FORCE_GUO) ? uy : (jy + tau * Fy) * inv;
+          const R vz = (FORCE == FORCE_GUO) ? uz : (jz + tau * Fz) * inv;
+          const R ks = R(1) - R(0.5) * om;
+          const R uF = ux * Fx + uy * Fy + uz * Fz;
           const R a0 = drho - R(1.5) * rho * (vx * vx + vy * vy + vz * vz);
           const R th = R(4.5) * (dE - drho * R(1.0 / 3.0));
           const R A[3] = {a0 - th, a0, a0 + th};
@@ -517,8 +548,18 @@ lb_fused_kernel(const KArgs a) {
             const R w = WT<R>(l) * om;
             const R sym = A[CLS(l)] + r45 * cv * cv;
             const R asym = r3 * cv;
-            Store<S>::st(fo + ((unsigned)l * N + own), om1 * f[l] + w * (sym + asym));
-            if (l != 0) Store<S>::st(fo + ((unsigned)OPP(l) * N + own), om1 * f[OPP(l)] + w * (sym - asym));
+            if constexpr (FORCE == FORCE_GUO) {
+              const R cF = R(CX(l)) * Fx + R(CY(l)) * Fy + R(CZ(l)) * Fz;
+              const R ws = WT<R>(l) * ks;
+              const R ssym = ws * (R(9) * cv * cF - R(3) * uF), sasym = ws * (R(3) * cF);
+              Store<S>::st(fo + ((unsigned)l * N + own), om1 * f[l] + w * (sym + asym) + (ssym + sasym));
+              if (l != 0)
+                Store<S>::st(fo + ((unsigned)OPP(l) * N + own),
+                             om1 * f[OPP(l)] + w * (sym - asym) + (ssym - sasym));
+            } else {
+              Store<S>::st(fo + ((unsigned)l * N + own), om1 * f[l] + w * (sym + asym));
+              if (l != 0) Store<S>::st(fo + ((unsigned)OPP(l) * N + own), om1 * f[OPP(l)] + w * (sym - asym));
+            }
           }
         }
         // g: BGK towards g^eq(rho, T, u) plus the counter term w_l S, S = -rho T div(u)/c_v.
@@ -551,14 +592,17 @@ lb_fused_kernel(const KArgs a) {
         if (a.uz_out) a.uz_out[own] = double(uz);
         if (a.T_out) a.T_out[own] = double(T);
         const double drho_ = double(rho), dT = double(T), duz = double(uz);
+        // U = c_v T + int_0^rho P_NI/s^2 ds: (G/4) e^{-2/rho}, or -T_v ln(1 - b rho) - a rho (vdW)
         if constexpr (sizeof(R) == 8) {
-          const double U = a.c_v * dT + 0.25 * a.G * exp(-2.0 / drho_);
+          const double U = a.c_v * dT + (VDW ? -kp.vT * log(1.0 - kp.vb * drho_) - kp.va * drho_
+                                             : 0.25 * a.G * exp(-2.0 / drho_));
           d_conv = drho_ * U * duz;
         } else {
           // FP32-compute forms: the node's term in float (relative error ~1e-7, far inside
           // these forms' tolerance; FP64 exp and division cost more than the step itself),
           // the sums over nodes in FP64
-          const R U = R(a.c_v) * T + R(0.25) * G * fexp(R(-2) * inv);
+          const R U = R(a.c_v) * T + (VDW ? -kp.vT * logf(R(1) - kp.vb * rho) - kp.va * rho
+                                          : R(0.25) * G * fexp(R(-2) * inv));
           d_conv = double(rho * U * uz);
         }
         d_T = dT; d_rho = drho_; d_E = double(E); d_mr = drho_; d_mT = dT;

@@ -13,9 +13,9 @@ struct PrecOps {
   cudaError_t (*init)(const KArgs&, const double*, const double*, cudaStream_t);
   cudaError_t (*pops)(const KArgs&, double*, double*, cudaStream_t);
   bool (*tile_ok)(int by);    // whether the tile height's shared-memory window fits a CTA
-  // launch description of the step kernel for a tile height: out = {threads per CTA, dynamic
-  // shared memory bytes, resident CTAs per SM, registers per thread}
-  cudaError_t (*info)(int by, int out[4]);
+  // launch description of the step kernel for a tile height and variant: out = {threads per
+  // CTA, dynamic shared memory bytes, resident CTAs per SM, registers per thread}
+  cudaError_t (*info)(int by, int var, int out[4]);
 };
 
 extern const PrecOps kOpsF64, kOpsF32, kOpsBF16, kOpsF16;
@@ -28,65 +28,87 @@ template <class S> struct OpsImpl {
   static constexpr bool STG = std::is_same<S, float>::value && TLBM_STAGE;
   template <int BY> static constexpr size_t smem() { return Geo<BY>::template smem_bytes<S, R, STG>(); }
   template <int BY> static constexpr bool fits() { return smem<BY>() + 1024 <= 227u * 1024u; }
-  template <int BY, int MODE> static cudaError_t attr() {
+  template <int BY, int MODE, int VAR = 0> static cudaError_t attr() {
     if constexpr (!fits<BY>()) {
       return cudaSuccess;
     } else {
-      return cudaFuncSetAttribute(lb_fused_kernel<S, BY, MODE>,
+      return cudaFuncSetAttribute(lb_fused_kernel<S, BY, MODE, VAR>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem<BY>());
     }
   }
+  template <int BY> static cudaError_t attr_by() {
+    cudaError_t e;
+    if ((e = attr<BY, MODE_STEP, 0>()) != cudaSuccess) return e;
+    if ((e = attr<BY, MODE_STEP, VAR_GUO>()) != cudaSuccess) return e;
+    if ((e = attr<BY, MODE_STEP, VAR_VDW>()) != cudaSuccess) return e;
+    if ((e = attr<BY, MODE_STEP, VAR_GUO | VAR_VDW>()) != cudaSuccess) return e;
+    if ((e = attr<BY, MODE_MOMENTS, 0>()) != cudaSuccess) return e;
+    return attr<BY, MODE_MOMENTS, VAR_VDW>();
+  }
   static cudaError_t prepare() {
     cudaError_t e;
-    if ((e = attr<4, MODE_STEP>()) != cudaSuccess) return e;
-    if ((e = attr<8, MODE_STEP>()) != cudaSuccess) return e;
-    if ((e = attr<16, MODE_STEP>()) != cudaSuccess) return e;
-    if ((e = attr<4, MODE_MOMENTS>()) != cudaSuccess) return e;
-    if ((e = attr<8, MODE_MOMENTS>()) != cudaSuccess) return e;
-    return attr<16, MODE_MOMENTS>();
+    if ((e = attr_by<4>()) != cudaSuccess) return e;
+    if ((e = attr_by<8>()) != cudaSuccess) return e;
+    return attr_by<16>();
   }
-  template <int BY> static cudaError_t info_by(int out[4]) {
+  template <int BY, int VAR> static cudaError_t info_var(int out[4]) {
     if constexpr (!fits<BY>()) {
       return cudaErrorInvalidConfiguration;
     } else {
       cudaFuncAttributes fa;
-      cudaError_t e = cudaFuncGetAttributes(&fa, lb_fused_kernel<S, BY, MODE_STEP>);
+      cudaError_t e = cudaFuncGetAttributes(&fa, lb_fused_kernel<S, BY, MODE_STEP, VAR>);
       if (e != cudaSuccess) return e;
       int n = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lb_fused_kernel<S, BY, MODE_STEP>, BX * BY,
-                                                        smem<BY>());
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lb_fused_kernel<S, BY, MODE_STEP, VAR>,
+                                                        BX * BY, smem<BY>());
       if (e != cudaSuccess) return e;
       out[0] = BX * BY; out[1] = (int)smem<BY>(); out[2] = n; out[3] = fa.numRegs;
       return cudaSuccess;
     }
   }
-  static cudaError_t info(int by, int out[4]) {
-    if (by == 4) return info_by<4>(out);
-    if (by == 8) return info_by<8>(out);
-    if (by == 16) return info_by<16>(out);
+  template <int BY> static cudaError_t info_by(int var, int out[4]) {
+    switch (var) {
+      case 0: return info_var<BY, 0>(out);
+      case VAR_GUO: return info_var<BY, VAR_GUO>(out);
+      case VAR_VDW: return info_var<BY, VAR_VDW>(out);
+      default: return info_var<BY, VAR_GUO | VAR_VDW>(out);
+    }
+  }
+  static cudaError_t info(int by, int var, int out[4]) {
+    if (by == 4) return info_by<4>(var, out);
+    if (by == 8) return info_by<8>(var, out);
+    if (by == 16) return info_by<16>(var, out);
     return cudaErrorInvalidValue;
   }
   static bool tile_ok(int by) {
     return (by == 4 && fits<4>()) || (by == 8 && fits<8>()) || (by == 16 && fits<16>());
   }
-  template <int BY, int MODE> static cudaError_t go(const KArgs& a, dim3 grid, cudaStream_t st) {
+  template <int BY, int MODE, int VAR> static cudaError_t go(const KArgs& a, dim3 grid, cudaStream_t st) {
     if constexpr (!fits<BY>()) {
       return cudaErrorInvalidConfiguration;
     } else {
-      lb_fused_kernel<S, BY, MODE><<<grid, dim3(BX, BY), smem<BY>(), st>>>(a);
+      lb_fused_kernel<S, BY, MODE, VAR><<<grid, dim3(BX, BY), smem<BY>(), st>>>(a);
       return cudaGetLastError();
     }
   }
-  static cudaError_t fused(const KArgs& a, int mode, int by, dim3 grid, cudaStream_t st) {
+  template <int BY> static cudaError_t go_by(const KArgs& a, int mode, dim3 grid, cudaStream_t st) {
+    const int var = variant_of(a.forcing, a.psi_kind);
     if (mode == MODE_STEP) {
-      if (by == 4) return go<4, MODE_STEP>(a, grid, st);
-      if (by == 8) return go<8, MODE_STEP>(a, grid, st);
-      if (by == 16) return go<16, MODE_STEP>(a, grid, st);
-    } else {
-      if (by == 4) return go<4, MODE_MOMENTS>(a, grid, st);
-      if (by == 8) return go<8, MODE_MOMENTS>(a, grid, st);
-      if (by == 16) return go<16, MODE_MOMENTS>(a, grid, st);
+      switch (var) {
+        case 0: return go<BY, MODE_STEP, 0>(a, grid, st);
+        case VAR_GUO: return go<BY, MODE_STEP, VAR_GUO>(a, grid, st);
+        case VAR_VDW: return go<BY, MODE_STEP, VAR_VDW>(a, grid, st);
+        default: return go<BY, MODE_STEP, VAR_GUO | VAR_VDW>(a, grid, st);
+      }
     }
+    // the moments pass has no collision: only the pseudopotential matters
+    if (var & VAR_VDW) return go<BY, MODE_MOMENTS, VAR_VDW>(a, grid, st);
+    return go<BY, MODE_MOMENTS, 0>(a, grid, st);
+  }
+  static cudaError_t fused(const KArgs& a, int mode, int by, dim3 grid, cudaStream_t st) {
+    if (by == 4) return go_by<4>(a, mode, grid, st);
+    if (by == 8) return go_by<8>(a, mode, grid, st);
+    if (by == 16) return go_by<16>(a, mode, grid, st);
     return cudaErrorInvalidValue;
   }
   static int blocks_for(int N) {

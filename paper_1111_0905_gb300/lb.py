@@ -16,6 +16,8 @@ import numpy as np
 LB_FP64, LB_FP32, LB_BF16_DEV, LB_FP16_DEV = 0, 1, 2, 3
 PRECISIONS = {"f64": LB_FP64, "f32": LB_FP32, "bf16dev": LB_BF16_DEV, "fp16dev": LB_FP16_DEV}
 STORAGE_BYTES = {LB_FP64: 8, LB_FP32: 4, LB_BF16_DEV: 2, LB_FP16_DEV: 2}
+LB_FORCE_SHIFT, LB_FORCE_GUO = 0, 1     # scheme variants (include/lb.h); 0 = the paper's
+LB_PSI_EXP, LB_PSI_VDW = 0, 1
 Q = 19
 
 _LIB_PATH = Path(__file__).resolve().parent / "libthermal_lbm.so"
@@ -38,6 +40,8 @@ class LbParams(ctypes.Structure):
         ("rho0", ctypes.c_double), ("T0", ctypes.c_double),
         ("precision", ctypes.c_int), ("nu_every", ctypes.c_int), ("check_every", ctypes.c_int),
         ("tile_y", ctypes.c_int), ("z_chunk", ctypes.c_int),
+        ("forcing", ctypes.c_int), ("psi_kind", ctypes.c_int),
+        ("vdw_a", ctypes.c_double), ("vdw_b", ctypes.c_double), ("vdw_T", ctypes.c_double),
     ]
 
 
@@ -62,6 +66,11 @@ class Params:
     check_every: int = 0
     tile_y: int = 0
     z_chunk: int = 0
+    forcing: int = 0          # LB_FORCE_SHIFT (the paper) or LB_FORCE_GUO
+    psi_kind: int = 0         # LB_PSI_EXP (the paper) or LB_PSI_VDW
+    vdw_a: float = 5.0 / 42.0
+    vdw_b: float = 2.0 / 21.0
+    vdw_T: float = 1.0 / 3.0
 
     def to_c(self) -> LbParams:
         return LbParams(*[getattr(self, f.name) for f in fields(self)])

@@ -10,7 +10,10 @@ from paper_1111_0905_gb300 import lb
 
 def oracle_params(p: lb.Params) -> lbm.Params:
     return lbm.Params(p.nx, p.ny, p.nz, p.tau_nu, p.tau_kappa, p.G, p.kappa, p.c_v, p.g_z,
-                      p.T_d, p.T_u)
+                      p.T_d, p.T_u,
+                      forcing="guo" if p.forcing == lb.LB_FORCE_GUO else "shift",
+                      psi_kind="vdw" if p.psi_kind == lb.LB_PSI_VDW else "exp",
+                      vdw_a=p.vdw_a, vdw_b=p.vdw_b, vdw_T=p.vdw_T)
 
 
 def oracle_run(p: lb.Params, rho, T, steps: int, nu_every: int = 0):

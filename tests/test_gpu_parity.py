@@ -308,3 +308,70 @@ def test_chunk_choice_and_occupancy(lblib, cuda):
             best = min(costs.values())
             zc_used = -(-n // info["grid"][1])
             assert costs[zc_used] == best, (n, info, costs)
+
+
+VARIANTS = [(lb.LB_FORCE_GUO, lb.LB_PSI_EXP), (lb.LB_FORCE_SHIFT, lb.LB_PSI_VDW),
+            (lb.LB_FORCE_GUO, lb.LB_PSI_VDW)]
+
+
+def _variant_cell(forcing, psi, precision, nx=20, ny=9, nz=11):
+    """Boiling cell of the variant: the paper's psi at rho = 1.30 (1 + 0.01 xi); the van der Waals
+    psi (a = 5/42, b = 2/21, T_v = T_m, critical point rho_c = 3.5, T_c = 10/27) at
+    rho = 3.5 (1 + 0.05 xi), inside its spinodal at T_m."""
+    w = config.boiling_cell(nx, nz=nz, ny=ny, precision=precision)
+    p = w.params
+    p.forcing, p.psi_kind = forcing, psi
+    rho, T = w.fields()
+    if psi == lb.LB_PSI_VDW:
+        rho, _ = synthetic.boiling_fields(nx, ny, nz, 3.5, p.T_d, p.T_u, 0.05)
+    return p, rho, T
+
+
+@pytest.mark.parametrize("forcing,psi", VARIANTS)
+def test_variant_parity_fp64(lblib, cuda, forcing, psi):
+    """Scheme variants (Guo forcing, van der Waals psi) against the oracle's variants, 1e-12."""
+    p, rho, T = _variant_cell(forcing, psi, lb.LB_FP64)
+    p.tile_y, p.z_chunk = 4, 3
+    _compare(p, rho, T, 15, 1e-12, nu_tol=1e-9)
+
+
+@pytest.mark.parametrize("forcing,psi", VARIANTS)
+def test_variant_parity_fp32(lblib, cuda, forcing, psi):
+    p, rho, T = _variant_cell(forcing, psi, lb.LB_FP32)
+    _compare(p, rho, T, 15, 1e-5, nu_tol=1e-3)
+
+
+def test_variant_parity_16bit(lblib, cuda):
+    """Guo forcing with the van der Waals psi in FP16 deviation storage: rho and T within 2e-3."""
+    p, rho, T = _variant_cell(lb.LB_FORCE_GUO, lb.LB_PSI_VDW, lb.LB_FP16_DEV)
+    lat = lb.Lattice(p, rho, T)
+    lat.step(15)
+    r, u, TT = lat.moments()
+    lat.close()
+    f, g, op, _ = oracle_run(p, rho, T, 15)
+    r_o, u_o, T_o = lbm.moments_out(f, g, op)
+    assert rel_err(r, r_o) < 2e-3 and rel_err(TT, T_o) < 2e-3
+
+
+def test_variant_arguments(lblib, cuda):
+    """Unknown variants, a van der Waals psi that is not real at an initial density, and the
+    adjoint of a variant are rejected with error codes."""
+    p, rho, T = _variant_cell(lb.LB_FORCE_SHIFT, lb.LB_PSI_VDW, lb.LB_FP64)
+    for field, value in (("forcing", 2), ("psi_kind", 7)):
+        q = lb.Params(**{**p.__dict__, field: value})
+        with pytest.raises(lb.LBError) as e:
+            lb.Lattice(q, rho, T)
+        assert e.value.code == -1
+    too_dense = rho.copy()
+    too_dense[0, 0, 0] = 0.999 * (1 - p.vdw_b * p.vdw_T / p.vdw_a) / p.vdw_b + 0.01
+    with pytest.raises(lb.LBError) as e:
+        lb.Lattice(p, too_dense, T)
+    assert e.value.code == -1
+    q = lb.Params(**{**p.__dict__, "G": 1.0})       # the van der Waals psi needs G < 0
+    with pytest.raises(lb.LBError):
+        lb.Lattice(q, rho, T)
+    lat = lb.Lattice(p, rho, T)
+    with pytest.raises(lb.LBError) as e:
+        lat.adjoint(4, 2)
+    assert e.value.code == -6
+    lat.close()

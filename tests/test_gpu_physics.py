@@ -6,6 +6,9 @@ classical limits), each with its oracle counterpart at small size in the CPU tes
   along the simulated coexistence curve (Fig. 1).
 - Static 3-D bubbles: Laplace law Delta P = 2 sigma / R (linear in 1/R).
 - Conduction below onset: linear T between the walls and Nu = 1.
+- Scheme variants: with Guo forcing the flat-interface densities do not depend on tau_nu and
+  sit on the Maxwell construction (the velocity shift's tau bias disappears); with the van der
+  Waals psi they follow the psi-rule of the pseudopotential (equal area in ln psi).
 - Rayleigh-Benard rolls (quasi-2-D, aspect 2.016 = the rigid-rigid critical wavelength): a roll
   perturbation decays at half the nominal onset Rayleigh number 1708 and grows into steady
   convection (Nu > 1.3) at twice it, with FP32 and FP64 agreeing on Nu.
@@ -178,3 +181,58 @@ def test_rayleigh_benard_rolls_decay_below_and_convect_above_onset():
         assert a1 > 100 * a0 and d["nonfinite"] == 0, (prec, a0, a1)
     assert nus[lb.LB_FP32] > 1.3 and nus[lb.LB_FP64] > 1.3, nus
     assert abs(nus[lb.LB_FP32] - nus[lb.LB_FP64]) < 2e-3 * nus[lb.LB_FP64], nus
+
+
+def _slab_variant(t, psi, forcing, tau, nz=96, steps=30000):
+    """Flat liquid slab at T = t T_c (isothermal walls), the paper's psi (G of the default cell)
+    or the van der Waals psi (a = 5/42, b = 2/21, T_v = T, G = -1); returns (rho_l, rho_g)."""
+    T0 = t * TC
+    A, B = 5.0 / 42.0, 2.0 / 21.0
+    if psi == lb.LB_PSI_EXP:
+        rg, rl = eos.coexistence(T0, G0)
+        G = G0
+    else:
+        rg, rl = eos.coexistence_vdw(T0, A, B, T0)
+        G = -1.0
+    p = lb.Params(nx=4, ny=4, nz=nz, tau_nu=tau, tau_kappa=1.0, G=G, kappa=0.24, g_z=0.0,
+                  T_d=T0, T_u=T0, forcing=forcing, psi_kind=psi, vdw_a=A, vdw_b=B, vdw_T=T0)
+    z = np.arange(nz) + 0.5
+    prof = 0.5 * (np.tanh((z - nz / 4) / 2.5) - np.tanh((z - 3 * nz / 4) / 2.5))
+    rho = np.broadcast_to((rg + (rl - rg) * prof)[:, None, None], (nz, 4, 4)).copy()
+    r, u, TT = _run(p, rho, np.full_like(rho, T0), steps)
+    return float(r[nz // 2].mean()), float(r[1].mean())
+
+
+def test_guo_forcing_removes_the_tau_bias_of_the_coexistence_densities():
+    """Paper's psi at T = 0.85 T_c. Guo forcing: rho_l, rho_g at tau_nu = 1, 1.5, 2 agree to
+    1e-3 and lie within 0.5 % of the Maxwell construction (measured 2.0729 / 0.49359 vs 2.0772 /
+    0.49266). Velocity shift: +1.1 % / +3.8 % at tau_nu = 1 growing to +6.0 % / +21 % at 2."""
+    rg, rl = eos.coexistence(0.85 * TC, G0)
+    guo = [_slab_variant(0.85, lb.LB_PSI_EXP, lb.LB_FORCE_GUO, tau) for tau in (1.0, 1.5, 2.0)]
+    for rl_m, rg_m in guo:
+        assert abs(rl_m / guo[0][0] - 1) < 1e-3 and abs(rg_m / guo[0][1] - 1) < 1e-3, guo
+        assert abs(rl_m / rl - 1) < 5e-3 and abs(rg_m / rg - 1) < 5e-3, (guo, rl, rg)
+    shift = [_slab_variant(0.85, lb.LB_PSI_EXP, lb.LB_FORCE_SHIFT, tau) for tau in (1.0, 2.0)]
+    assert shift[0][0] / rl - 1 > 0.005 and shift[1][0] / rl - 1 > 2 * (shift[0][0] / rl - 1), shift
+    assert shift[1][1] / rg - 1 > 0.1, shift
+
+
+def test_vdw_psi_coexistence_follows_the_psi_rule():
+    """Van der Waals psi at T = 0.85 T_c with Guo forcing: tau-independent (tau_nu = 1.5, 2) and
+    closer to the psi-rule (equal area in ln psi: rho_g 1.0301, rho_l 6.2998) than to Maxwell's
+    rule of the same pressure (1.1191, 6.3250); measured 1.0634 / 6.2750."""
+    T0 = 0.85 * TC
+    A, B = 5.0 / 42.0, 2.0 / 21.0
+    res = [_slab_variant(0.85, lb.LB_PSI_VDW, lb.LB_FORCE_GUO, tau) for tau in (1.5, 2.0)]
+    assert abs(res[0][0] / res[1][0] - 1) < 1e-3 and abs(res[0][1] / res[1][1] - 1) < 1e-3, res
+    rl_m, rg_m = res[1]
+    P = lambda r: eos.pressure_vdw(r, T0, A, B, T0)
+    psi = lambda r: r * math.sqrt(2.0 * (A - B * T0 / (1 - B * r)))
+    dpsi = lambda r: (psi(r + 1e-6) - psi(r - 1e-6)) / 2e-6
+    mg, ml = eos.coexistence_vdw(T0, A, B, T0)
+    from scipy.optimize import brentq
+    lo = brentq(lambda r: eos.dP_drho_vdw(r, T0, A, B, T0), 0.05, 3.5)
+    hi = brentq(lambda r: eos.dP_drho_vdw(r, T0, A, B, T0), 3.5, 0.999 / B)
+    eg, el = eos.coexistence_psi_rule(P, psi, dpsi, lo, hi, 0.0, [mg, ml])
+    assert abs(rg_m / eg - 1) < 0.05 and abs(rl_m / el - 1) < 0.01, (res, eg, el)
+    assert abs(rg_m / eg - 1) < abs(rg_m / mg - 1), (rg_m, eg, mg)
