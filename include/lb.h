@@ -176,6 +176,16 @@ int lb_histogram_T_rho(lb_ctx* ctx, int z_lo, int z_hi, int nT, double T_lo, dou
 int lb_structure_functions(lb_ctx* ctx, int rmax, int z_lo, int z_hi, double* S2_uz, double* S4_uz,
                            double* S2_T, double* S4_T);
 
+/* lb_heat_flux_pdf -- statistics of the local convective heat flux q = rho U u_z (U = c_v T plus the
+ * non-ideal internal energy; the bulk term of Nu in Eq. (4), whose pdf in the bulk is the inset of
+ * Fig. 2) over the planes [z_lo, z_hi): counts (host uint64 [nbins], 1 <= nbins <= 12288) of the
+ * nodes with q_lo <= q < q_hi, bin = floor((q - q_lo)/(q_hi - q_lo) nbins), and stats (host
+ * double [3]) = number of nodes, mean and variance of q over every node of the planes (FP64,
+ * fixed-order sums, variance from the deviations from the mean). Either output may be NULL.
+ * Synchronises. Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+int lb_heat_flux_pdf(lb_ctx* ctx, int z_lo, int z_hi, int nbins, double q_lo, double q_hi,
+                     unsigned long long* counts, double* stats);
+
 /* lb_save / lb_load -- checkpoint of (parameters, step count, populations in their storage
  * precision) to a raw binary file with a header and a 64-bit FNV-1a checksum of the payload.
  * lb_load requires a context created with the same grid and precision and replaces its state.

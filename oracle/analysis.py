@@ -54,3 +54,22 @@ def structure_functions(uz, T, rmax, z_lo, z_hi):
             out[f"S2_{name}"][r - 1] = (d ** 2).mean().item()
             out[f"S4_{name}"][r - 1] = (d ** 4).mean().item()
     return out
+
+
+def heat_flux_pdf(f, g, p: lbm.Params, z_lo, z_hi, nbins, q_range):
+    """Local convective heat flux q = rho U u_z (the bulk part of Nu, Eq. (4) and Fig. 2 inset)
+    over the planes [z_lo, z_hi): counts of lo <= q < hi with bin = floor((q - lo)/(hi - lo) n),
+    and (number of nodes, mean, variance) of q over every node of the planes."""
+    rho, j, T, F, u_eq, u = lbm.macroscopic(f, g, p)
+    U = lbm.internal_energy(rho, T, p)
+    q = (rho * U * u[2])[z_lo:z_hi].reshape(-1).numpy()
+    counts = np.zeros(nbins, dtype=np.uint64)
+    lo, hi = q_range
+    for v in q:
+        if lo <= v < hi:
+            counts[min(int(math.floor((v - lo) / (hi - lo) * nbins)), nbins - 1)] += 1
+    n = q.size
+    mean = float(np.sum(q) / n)
+    var = float(np.sum((q - mean) ** 2) / n)
+    return counts, (float(n), mean, var)
+

@@ -113,6 +113,60 @@ __global__ void structure_kernel(const double* __restrict__ uz, const double* __
   }
 }
 
+// Local convective heat flux q = rho U u_z, U = c_v T + U_NI(rho) (the bulk term of Nu, Eq. (4)).
+struct FluxArgs {
+  double c_v, G, va, vb, vT;
+  int psi_kind;
+};
+__device__ __forceinline__ double flux_q(double r, double t, double w, const FluxArgs& fa) {
+  const double uni = (fa.psi_kind == PSI_VDW) ? -fa.vT * log(1.0 - fa.vb * r) - fa.va * r
+                                              : 0.25 * fa.G * exp(-2.0 / r);
+  return r * (fa.c_v * t + uni) * w;
+}
+
+// Pass 1 of the heat-flux pdf: counts of lo <= q < hi in n bins (shared counts, global integer
+// atomics) and this block's sum of q (fixed thread-to-node assignment and reduction order).
+__global__ void flux_hist_kernel(const double* __restrict__ rho, const double* __restrict__ uz,
+                                 const double* __restrict__ T, size_t begin, size_t end, FluxArgs fa,
+                                 int nb, double lo, double hi, unsigned long long* __restrict__ counts,
+                                 double* __restrict__ part) {
+  extern __shared__ unsigned int hq[];
+  __shared__ double sh[32];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hq[b] = 0u;
+  __syncthreads();
+  double s = 0.0;
+  for (size_t k = begin + blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < end;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const double q = flux_q(rho[k], T[k], uz[k], fa);
+    s += q;
+    if (q >= lo && q < hi) {
+      int b = (int)floor((q - lo) / (hi - lo) * nb);
+      b = b < nb - 1 ? b : nb - 1;
+      atomicAdd(&hq[b], 1u);
+    }
+  }
+  const double bs = block_sum(s, sh);
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    if (hq[b]) atomicAdd(&counts[b], (unsigned long long)hq[b]);
+  if (threadIdx.x == 0) part[blockIdx.x] = bs;
+}
+
+// Pass 2: this block's sum of (q - mean)^2.
+__global__ void flux_var_kernel(const double* __restrict__ rho, const double* __restrict__ uz,
+                                const double* __restrict__ T, size_t begin, size_t end, FluxArgs fa,
+                                double mean, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (size_t k = begin + blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < end;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const double d = flux_q(rho[k], T[k], uz[k], fa) - mean;
+    s += d * d;
+  }
+  const double bs = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = bs;
+}
+
 }  // namespace ana
 }  // namespace tlbm
 
@@ -211,5 +265,44 @@ extern "C" int lb_structure_functions(lb_ctx* c, int rmax, int z_lo, int z_hi, d
     if (S2_T) S2_T[r] = s[2] / cnt;
     if (S4_T) S4_T[r] = s[3] / cnt;
   }
+  return LB_OK;
+}
+
+extern "C" int lb_heat_flux_pdf(lb_ctx* c, int z_lo, int z_hi, int nbins, double q_lo, double q_hi,
+                                unsigned long long* counts, double* stats) {
+  if (!c) return LB_EINVAL;
+  if (z_lo < 0 || z_hi > c->p.nz || z_lo >= z_hi || nbins < 1 || nbins > 12288 || !(q_hi > q_lo))
+    return lb_fail(c, LB_EINVAL, "heat-flux pdf ranges");
+  double *rho, *ux, *uy, *uz, *T;
+  int rc = fields_on_device(c, &rho, &ux, &uy, &uz, &T);
+  if (rc) return rc;
+  const int blocks = 304;
+  DevBuf cnt, part;
+  if (cudaMalloc(&cnt.p, (size_t)nbins * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&part.p, 2 * blocks * sizeof(double)) != cudaSuccess)
+    return lb_fail(c, LB_ENOMEM, "heat-flux pdf");
+  LB_CU(c, cudaMemsetAsync(cnt.p, 0, (size_t)nbins * sizeof(unsigned long long), c->stream));
+  const size_t plane = (size_t)c->plane, begin = (size_t)z_lo * plane, end = (size_t)z_hi * plane;
+  const ana::FluxArgs fa = {c->p.c_v, c->p.G, c->p.vdw_a, c->p.vdw_b, c->p.vdw_T, c->p.psi_kind};
+  double* pd = static_cast<double*>(part.p);
+  ana::flux_hist_kernel<<<blocks, 256, (size_t)nbins * sizeof(unsigned int), c->stream>>>(
+      rho, uz, T, begin, end, fa, nbins, q_lo, q_hi, static_cast<unsigned long long*>(cnt.p), pd);
+  LB_CU(c, cudaGetLastError());
+  std::vector<double> h(blocks);
+  LB_CU(c, cudaMemcpyAsync(h.data(), pd, blocks * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CU(c, cudaStreamSynchronize(c->stream));
+  const double n = (double)(end - begin);
+  double s = 0.0;
+  for (int b = 0; b < blocks; ++b) s += h[b];
+  const double mean = s / n;
+  ana::flux_var_kernel<<<blocks, 256, 0, c->stream>>>(rho, uz, T, begin, end, fa, mean, pd + blocks);
+  LB_CU(c, cudaGetLastError());
+  LB_CU(c, cudaMemcpyAsync(h.data(), pd + blocks, blocks * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (counts)
+    LB_CU(c, cudaMemcpyAsync(counts, cnt.p, (size_t)nbins * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  LB_CU(c, cudaStreamSynchronize(c->stream));
+  double v = 0.0;
+  for (int b = 0; b < blocks; ++b) v += h[b];
+  if (stats) { stats[0] = n; stats[1] = mean; stats[2] = v / n; }
   return LB_OK;
 }

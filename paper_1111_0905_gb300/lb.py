@@ -27,7 +27,7 @@ _lib = None
 EXPORTS = ("lb_init", "lb_step", "lb_adjoint_step", "lb_profiles", "lb_histogram_T_rho",
            "lb_structure_functions", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
            "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error",
-           "lb_nusselt_fields_noalloc", "lb_launch_info")
+           "lb_nusselt_fields_noalloc", "lb_launch_info", "lb_heat_flux_pdf")
 NOALLOC_MAX_NZ = 8192
 
 
@@ -136,6 +136,8 @@ def load_library():
     lib.lb_nusselt_fields_noalloc.restype = I
     lib.lb_launch_info.argtypes = [P, P]
     lib.lb_launch_info.restype = I
+    lib.lb_heat_flux_pdf.argtypes = [P, I, I, I, D, D, P, P]
+    lib.lb_heat_flux_pdf.restype = I
     _lib = lib
     return lib
 
@@ -256,6 +258,14 @@ class Lattice:
                                                 nrho, rho_range[0], rho_range[1], _ptr(counts)),
                     "lb_histogram_T_rho")
         return counts
+
+    def heat_flux_pdf(self, z_lo, z_hi, nbins, q_range):
+        """(uint64 counts [nbins], (n, mean, variance)) of q = rho U u_z over planes [z_lo, z_hi)."""
+        counts = np.zeros(nbins, dtype=np.uint64)
+        stats = np.zeros(3, dtype=np.float64)
+        self._check(self.lib.lb_heat_flux_pdf(self.ctx, z_lo, z_hi, nbins, q_range[0], q_range[1],
+                                              _ptr(counts), _ptr(stats)), "lb_heat_flux_pdf")
+        return counts, (float(stats[0]), float(stats[1]), float(stats[2]))
 
     def structure_functions(self, rmax, z_lo, z_hi):
         """dict of S2/S4 of u_z and T for horizontal increments r = 1..rmax."""

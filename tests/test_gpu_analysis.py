@@ -1,4 +1,4 @@
-"""Parity of the statistics entry points (lb_profiles, lb_histogram_T_rho,
+"""Parity of the statistics entry points (lb_profiles, lb_histogram_T_rho, lb_heat_flux_pdf,
 lb_structure_functions) with the oracle's, on the same evolved boiling cell."""
 import numpy as np
 import pytest
@@ -53,3 +53,18 @@ def test_structure_functions_match_oracle(evolved):
     ref = analysis.structure_functions(u_o[2].numpy(), T_o.numpy(), 10, 3, 17)
     for k in ref:
         assert np.abs(got[k] - ref[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
+
+
+def test_heat_flux_pdf_matches_oracle(evolved):
+    """lb_heat_flux_pdf: counts of q = rho U u_z in 20 bins over the bulk planes and its mean and
+    variance, against the oracle's."""
+    lat, f, g, op = evolved
+    _, (n_o, mean_o, var_o) = analysis.heat_flux_pdf(f, g, op, 3, 17, 1, (-1.0, 1.0))
+    sd = var_o ** 0.5
+    rng = (mean_o - 3 * sd, mean_o + 3 * sd)
+    got, (n, mean, var) = lat.heat_flux_pdf(3, 17, 20, rng)
+    ref, _ = analysis.heat_flux_pdf(f, g, op, 3, 17, 20, rng)
+    assert n == n_o == 14 * 16 * 24
+    assert abs(mean - mean_o) <= 1e-10 * sd and abs(var / var_o - 1) <= 1e-10
+    diff = int(np.abs(got.astype(np.int64) - ref.astype(np.int64)).sum())
+    assert diff <= 2 and ref.sum() > 0.8 * n, (got, ref)

@@ -51,3 +51,29 @@ def test_profiles_of_a_state_at_rest():
     assert torch.allclose(T_z, T[:, 0, 0], rtol=1e-14, atol=0)
     assert torch.allclose(r_z, rho[:, 0, 0], rtol=1e-14, atol=0)
     assert PD_z.abs().max() < 1e-15
+
+
+def test_heat_flux_pdf_of_a_state_at_rest_and_of_a_shear():
+    """At rest q = rho U u_z = 0 everywhere (one bin, zero mean and variance); for a state with
+    u_z = A sin(2 pi x / L) at uniform rho, T the mean is 0, the variance (rho U A)^2 / 2, and the
+    counts follow the arcsine law of the sampled sinusoid."""
+    import torch
+    from oracle import analysis, lbm
+    L = 16
+    p = lbm.Params(L, 2, 3, 1.0, 1.0, -2.7, 0.05, T_d=1 / 3, T_u=1 / 3)
+    rho = torch.full((3, 2, L), 1.7, dtype=torch.float64)
+    T = torch.full_like(rho, 1 / 3)
+    f, g = lbm.init_state(rho, T, p)
+    counts, (n, mean, var) = analysis.heat_flux_pdf(f, g, p, 0, 3, 4, (-1.0, 1.0))
+    assert n == 3 * 2 * L and mean == 0.0 and var == 0.0 and counts[2] == n
+    A = 1e-3
+    u = torch.zeros((3,) + tuple(rho.shape), dtype=torch.float64)
+    u[2] = A * torch.sin(2 * math.pi * torch.arange(L, dtype=torch.float64) / L)[None, None, :]
+    # a state whose physical velocity is u: no force at uniform rho (F = rho g_z = 0)
+    f = lbm.equilibrium_f(rho, u, T)
+    g = lbm.equilibrium_g(rho, T, u, p.lam)
+    U = float(lbm.internal_energy(rho, T, p)[0, 0, 0])
+    qmax = 1.7 * U * A
+    counts, (n, mean, var) = analysis.heat_flux_pdf(f, g, p, 0, 3, 8, (-qmax * 1.0001, qmax * 1.0001))
+    assert abs(mean) < 1e-18 and abs(var / (0.5 * qmax ** 2) - 1) < 1e-12
+    assert counts.sum() == n and counts[0] == counts[-1] and counts[0] > counts[3]
