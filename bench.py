@@ -206,6 +206,8 @@ def run_ours(args):
     for form in form_list:
         w = workload(form)
         p = w.params
+        if args.only:
+            p.nu_every = args.nu_every
         N = p.nx * p.ny * p.nz
         rho, T = w.fields()
         rho_d = torch.from_numpy(rho).cuda()
@@ -290,6 +292,7 @@ def run_ours(args):
     # the sizes the HBM target is stated at (256^3, 512^3), same kernel, paper-geometry boiling cell
     sizes = {} if args.no_sizes else size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws)
     variants = {} if args.no_sizes else variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws)
+    diagnostics = diagnostics_cost(lb, torch, max_over_ranks, barrier, results[main_form]["ms_per_step"])
 
     main = results[main_form]
     src_hash = kernel_src_hash()
@@ -312,7 +315,8 @@ def run_ours(args):
                "data": "synthetic (seeded SplitMix64 fields; no dataset)",
                "config": config_dict(w, main_form), "roofline": roofline, "cpu_baseline": cpu,
                "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_summary,
-               "forms": results, "sizes": sizes, "variants": variants, "kernel_src_hash": src_hash}
+               "forms": results, "sizes": sizes, "variants": variants, "diagnostics": diagnostics,
+               "kernel_src_hash": src_hash}
         print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
@@ -351,6 +355,30 @@ def size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
                                     "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                     "workload": w.name, "launch": launch}
     return out
+
+
+def diagnostics_cost(lb, torch, max_over_ranks, barrier, ms_step: float) -> dict:
+    """Cost of sampling Nu(z) and the health values every step (nu_every = 1: one moments pass
+    and one finalisation per step) on the FP32 128^3 cell, 200 timed steps after 10 warm-up."""
+    w = workload("f32")
+    p = w.params
+    p.nu_every = 1
+    rho, T = w.fields()
+    lat = lb.Lattice(p, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+    lat.step(10)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    K = 200
+    e0.record()
+    lat.step(K)
+    e1.record()
+    e1.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1)) / K
+    lat.close()
+    return {"nu_every": 1, "ms_per_step": ms, "ms_per_sample": ms - ms_step,
+            "step_only_ms": ms_step}
 
 
 def variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
@@ -472,6 +500,8 @@ def main():
     ap.add_argument("--no-sizes", action="store_true", help="skip the 256^3/512^3 measurements")
     ap.add_argument("--only", choices=list(FORMS), help="time one form of the 128^3 cell only "
                     "(no errors, e2e or baselines; for profiling)")
+    ap.add_argument("--nu-every", type=int, default=0, help="with --only: sample Nu every n steps "
+                    "inside the timed steps (the diagnostics path)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

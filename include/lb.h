@@ -120,10 +120,11 @@ int lb_moments(lb_ctx* ctx, double* rho, double* ux, double* uy, double* uz, dou
 
 /* lb_nusselt -- layer heat flux of Eq. (4) as a Nusselt number,
  * Nu(z) = <rho U u_z - kappa dT/dz>_{x,y} / (kappa (T_d - T_u)/nz), U = c_v T + (G/4) e^{-2/rho}
- * (Eq. (2)), dT/dz by central differences with wall ghosts 2 T_wall - T. Host outputs:
- * *nu_mean = mean over z; nu_z (may be NULL) = nz values; *nu_time_avg (may be NULL) = mean of
- * the Nu_mean samples accumulated by lb_step with nu_every > 0 (NaN if none).
- * FP64 warp-shuffle reductions on the device; synchronises. Errors: LB_EINVAL, LB_ECUDA. */
+ * (Eq. (2); for the van der Waals psi U = c_v T - T_v ln(1 - b rho) - a rho), dT/dz by central
+ * differences with wall ghosts 2 T_wall - T. Host outputs: *nu_mean = mean over z; nu_z (may be
+ * NULL) = nz values; *nu_time_avg (may be NULL) = mean of the Nu_mean samples accumulated by
+ * lb_step with nu_every > 0 (NaN if none). Warp sums in the compute precision, FP64 across warps,
+ * tiles and planes in a fixed order (deterministic); synchronises. Errors: LB_EINVAL, LB_ECUDA. */
 int lb_nusselt(lb_ctx* ctx, double* nu_mean, double* nu_z, double* nu_time_avg);
 
 /* lb_adjoint_step -- advance nsteps steps from the current state (as lb_step) and return the

@@ -311,6 +311,28 @@ template <> __device__ __forceinline__ float cvt<__half, float>(__half v) { retu
 
 // Resident CTAs per SM the register allocation must allow: 512 threads per SM for the FP32 and
 // 16-bit forms (128 registers a thread); the FP64 form is limited by its shared memory anyway.
+// Moments mode: per-warp partials of the last two collided planes (slot z & 1), combined over
+// the warps by warp 0 after the next barrier (static shared memory of the moments kernels only).
+template <class R, int BY> __device__ __forceinline__ R (*moments_red())[7][BY] {
+  __shared__ R red[2][7][BY];
+  return red;
+}
+// lanes 0..6 of warp 0 combine partial k of plane z over the BY warps, in warp order, in FP64
+template <class R, int BY>
+__device__ __forceinline__ void moments_combine(const KArgs& a, int z, int tile, int tid) {
+  R (*red)[7][BY] = moments_red<R, BY>();
+  if (tid < NPART) {
+    double acc = 0.0;
+    if (tid < 7) {
+      const R* v = red[z & 1][tid];
+      acc = double(v[0]);
+      for (int w = 1; w < BY; ++w)
+        acc = (tid == 4 || tid == 5) ? fmin(acc, double(v[w])) : acc + double(v[w]);
+    }
+    a.part[((size_t)z * a.ntiles + tile) * NPART + tid] = acc;
+  }
+}
+
 template <class S, int BY> struct MinBlocks { static constexpr int v = 512 / (BX * BY) > 0 ? 512 / (BX * BY) : 1; };
 template <int BY> struct MinBlocks<double, BY> { static constexpr int v = 1; };
 
@@ -435,6 +457,10 @@ lb_fused_kernel(const KArgs a) {
       }
     }
     __syncthreads();
+    if constexpr (MODE == MODE_MOMENTS) {
+      // the partials of the plane collided in the previous iteration are complete
+      if (a.part != nullptr && p - 3 >= z0 && p - 3 < z1) moments_combine<R, BY>(a, p - 3, tile, tid);
+    }
     // ---------------- U: F and u = (j + F/2)/rho of plane q = p-1 ----------------
     {
       const int q = p - 1;
@@ -475,8 +501,11 @@ lb_fused_kernel(const KArgs a) {
     // No barrier before C: of what this U stage writes, C reads u of plane p-1 and F only at the
     // thread's own node (written by itself); its ring reads are of planes finished one barrier ago.
     // ---------------- C: collide plane z = p-2 ----------------
-    // moments-mode partials of this thread's node (neutral values when it has none)
-    double d_conv = 0.0, d_T = 0.0, d_rho = 0.0, d_E = 0.0, d_mr = 1e300, d_mT = 1e300, d_bad = 0.0;
+    // moments-mode partials of this thread's node in the compute precision (neutral values when
+    // it has none); warp sums in the compute precision, then FP64 across warps, tiles and planes
+    R d_conv = R(0), d_T = R(0), d_rho = R(0), d_E = R(0);
+    R d_mr = R(sizeof(R) == 8 ? 1e300 : 3.0e38), d_mT = d_mr;
+    bool d_bad = false;
     if (cplane && cvalid) {
       const unsigned own = (unsigned)z * plane + (unsigned)(crow[1] + ccol[1]);
       const int t = ty * BX + tx;
@@ -591,53 +620,47 @@ lb_fused_kernel(const KArgs a) {
         if (a.uy_out) a.uy_out[own] = double(uy);
         if (a.uz_out) a.uz_out[own] = double(uz);
         if (a.T_out) a.T_out[own] = double(T);
-        const double drho_ = double(rho), dT = double(T), duz = double(uz);
         // U = c_v T + int_0^rho P_NI/s^2 ds: (G/4) e^{-2/rho}, or -T_v ln(1 - b rho) - a rho (vdW)
         if constexpr (sizeof(R) == 8) {
-          const double U = a.c_v * dT + (VDW ? -kp.vT * log(1.0 - kp.vb * drho_) - kp.va * drho_
-                                             : 0.25 * a.G * exp(-2.0 / drho_));
-          d_conv = drho_ * U * duz;
+          const double U = a.c_v * T + (VDW ? -kp.vT * log(1.0 - kp.vb * rho) - kp.va * rho
+                                            : 0.25 * a.G * exp(-2.0 / rho));
+          d_conv = rho * U * uz;
         } else {
-          // FP32-compute forms: the node's term in float (relative error ~1e-7, far inside
-          // these forms' tolerance; FP64 exp and division cost more than the step itself),
-          // the sums over nodes in FP64
+          // FP32-compute forms: the node's term in float (relative error ~1e-7, far inside these
+          // forms' tolerance; on GB300 FP64 instructions cost more than the step itself)
           const R U = R(a.c_v) * T + (VDW ? -kp.vT * logf(R(1) - kp.vb * rho) - kp.va * rho
                                           : R(0.25) * G * fexp(R(-2) * inv));
-          d_conv = double(rho * U * uz);
+          d_conv = rho * U * uz;
         }
-        d_T = dT; d_rho = drho_; d_E = double(E); d_mr = drho_; d_mT = dT;
-        d_bad = (isfinite(drho_) && isfinite(dT) && isfinite(double(ux)) && isfinite(double(uy)) &&
-                 isfinite(duz)) ? 0.0 : 1.0;
+        d_T = T; d_rho = rho; d_E = E; d_mr = rho; d_mT = T;
+        d_bad = !(isfinite(rho) && isfinite(T) && isfinite(ux) && isfinite(uy) && isfinite(uz));
       }
     }
     if constexpr (MODE == MODE_MOMENTS) {
       if (a.part != nullptr && cplane) {
-        // FP64 warp-shuffle reduction of the plane partials, then across the BY warps
-        __shared__ double red[7][BY];
+        // warp-shuffle reduction of the plane partials in the compute precision (the
+        // non-finite count by ballot); combined over the warps in FP64 after the next barrier
+        R (*red)[7][BY] = moments_red<R, BY>();
         d_conv = warp_sum(d_conv); d_T = warp_sum(d_T); d_rho = warp_sum(d_rho);
-        d_E = warp_sum(d_E); d_mr = warp_min(d_mr); d_mT = warp_min(d_mT); d_bad = warp_sum(d_bad);
+        d_E = warp_sum(d_E); d_mr = warp_min(d_mr); d_mT = warp_min(d_mT);
+        const int nbad = __popc(__ballot_sync(0xffffffffu, d_bad));
         if (tx == 0) {
-          red[0][ty] = d_conv; red[1][ty] = d_T; red[2][ty] = d_rho; red[3][ty] = d_E;
-          red[4][ty] = d_mr; red[5][ty] = d_mT; red[6][ty] = d_bad;
-        }
-        __syncthreads();
-        if (tid == 0) {
-          double acc[7];
-          for (int k = 0; k < 7; ++k) acc[k] = red[k][0];
-          for (int w = 1; w < BY; ++w) {
-            for (int k = 0; k < 4; ++k) acc[k] += red[k][w];
-            acc[4] = fmin(acc[4], red[4][w]); acc[5] = fmin(acc[5], red[5][w]);
-            acc[6] += red[6][w];
-          }
-          double* out = a.part + ((size_t)z * a.ntiles + tile) * NPART;
-          for (int k = 0; k < 7; ++k) out[k] = acc[k];
-          out[7] = 0.0;
+          R* r = &red[z & 1][0][ty];
+          r[0] = d_conv; r[BY] = d_T; r[2 * BY] = d_rho; r[3 * BY] = d_E; r[4 * BY] = d_mr;
+          r[5 * BY] = d_mT; r[6 * BY] = R(nbad);
         }
       }
     }
     // With D = 3 the next M stage refills the psi slot that this U stage read and the rho/j
     // (and f-cache) slot that this C stage read.
     if (D == 3) __syncthreads();
+  }
+  if constexpr (MODE == MODE_MOMENTS) {
+    // the chunk's last plane
+    if (a.part != nullptr) {
+      __syncthreads();
+      moments_combine<R, BY>(a, z1 - 1, tile, tid);
+    }
   }
 }
 
