@@ -367,8 +367,11 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
   double* jacc = static_cast<double*>(acc.p);
   LB_CU(c, cudaMemsetAsync(part, 0, (size_t)kBlocks * P_COUNT * sizeof(double), st));
   LB_CU(c, cudaMemsetAsync(jacc, 0, 2 * sizeof(double), st));
+  const int frc = flush_sample(c);    // a Nu sample due for the time average of lb_nusselt
+  if (frc) return frc;
 
-  // forward: checkpoints every K steps, J from the Nu of states 1..N
+  // forward: checkpoints every K steps, J from the Nu of states 1..N (the sample of state n is
+  // taken by the launch of step n -> n+1; the last state's by a moments pass)
   const dim3 grid = fused_grid(c);
   for (long long n = 0; n < nsteps; ++n) {
     if (n % K == 0) {
@@ -377,9 +380,18 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
       LB_CU(c, cudaMemcpyAsync(dst + pbytes, c->g[c->cur], pbytes, cudaMemcpyDeviceToDevice, st));
     }
     KArgs a = make_args(c);
-    LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, st));
+    if (n >= 1) {
+      a.part = c->part;
+      LB_CU(c, c->ops->fused(a, MODE_STEP_DIAG, c->by, grid, st));
+      const int rc = finalize_diag(c, jacc);
+      if (rc != LB_OK) return rc;
+    } else {
+      LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, st));
+    }
     c->cur ^= 1;
     c->step += 1;
+  }
+  {
     const int rc = run_diag_acc(c, jacc);
     if (rc != LB_OK) return rc;
   }

@@ -164,18 +164,27 @@ void free_all(lb_ctx* c) {
 
 // Moments pass into the plane partials, then Nu(z) and the global health values into diag;
 // Nu_mean is added to acc[0] (and 1 to acc[1]) when acc is not null.
-int run_diag_acc(lb_ctx* c, double* acc) {
-  KArgs a = make_args(c);
-  a.part = c->part;
-  LB_CU(c, c->ops->fused(a, MODE_MOMENTS, c->by, fused_grid(c), c->stream));
-  const int nz = c->p.nz;
+int finalize_diag(lb_ctx* c, double* acc) {
   lb_diag_finalize<<<1, 1024, 0, c->stream>>>(
-      c->part, nz, c->ntiles, c->p.nx * c->p.ny, c->p.kappa, c->p.T_d, c->p.T_u, c->diag, acc);
+      c->part, c->p.nz, c->ntiles, c->p.nx * c->p.ny, c->p.kappa, c->p.T_d, c->p.T_u, c->diag, acc);
   LB_CU(c, cudaGetLastError());
   return LB_OK;
 }
 
+int run_diag_acc(lb_ctx* c, double* acc) {
+  KArgs a = make_args(c);
+  a.part = c->part;
+  LB_CU(c, c->ops->fused(a, MODE_MOMENTS, c->by, fused_grid(c), c->stream));
+  return finalize_diag(c, acc);
+}
+
 int run_diag(lb_ctx* c, bool accumulate) { return run_diag_acc(c, accumulate ? c->nu_acc : nullptr); }
+
+int flush_sample(lb_ctx* c) {
+  if (!c->sample_pending) return LB_OK;
+  c->sample_pending = false;
+  return run_diag(c, true);
+}
 
 namespace {
 
@@ -368,17 +377,27 @@ int lb_step(lb_ctx* c, long long nsteps) {
   if (!c) return LB_EINVAL;
   if (nsteps < 0) return lb_fail(c, LB_EINVAL, "nsteps < 0");
   const dim3 grid = fused_grid(c);
+  // a Nu sample of state n is taken by the launch of step n -> n+1 (the paper's scheme; the
+  // variants take it with a separate moments pass)
+  const bool fuse = variant_of(c->p.forcing, c->p.psi_kind) == 0;
   for (long long s = 0; s < nsteps; ++s) {
     KArgs a = make_args(c);
-    LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, c->stream));
+    if (c->sample_pending && fuse) {
+      a.part = c->part;
+      LB_CU(c, c->ops->fused(a, MODE_STEP_DIAG, c->by, grid, c->stream));
+      c->sample_pending = false;
+      const int rc = finalize_diag(c, c->nu_acc);
+      if (rc) return rc;
+    } else {
+      const int rc = flush_sample(c);
+      if (rc) return rc;
+      LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, c->stream));
+    }
     c->cur ^= 1;
     c->step += 1;
-    if (c->p.nu_every > 0 && c->step % c->p.nu_every == 0) {
-      int rc = run_diag(c, true);
-      if (rc) return rc;
-    }
+    if (c->p.nu_every > 0 && c->step % c->p.nu_every == 0) c->sample_pending = true;
     if (c->p.check_every > 0 && c->step % c->p.check_every == 0) {
-      int rc = run_diag(c, false);
+      int rc = c->sample_pending ? flush_sample(c) : run_diag(c, false);
       if (rc) return rc;
       double h[4];
       LB_CU(c, cudaMemcpyAsync(h, c->diag + c->p.nz, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -415,7 +434,7 @@ int lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* uz, doubl
 
 int lb_nusselt(lb_ctx* c, double* nu_mean, double* nu_z, double* nu_time_avg) {
   if (!c || !nu_mean) return c ? lb_fail(c, LB_EINVAL, "nu_mean is null") : LB_EINVAL;
-  int rc = run_diag(c, false);
+  int rc = c->sample_pending ? flush_sample(c) : run_diag(c, false);
   if (rc) return rc;
   const int nz = c->p.nz;
   std::vector<double> h(nz + 1);
@@ -431,7 +450,7 @@ int lb_nusselt(lb_ctx* c, double* nu_mean, double* nu_z, double* nu_time_avg) {
 
 int lb_diagnostics(lb_ctx* c, double out[5]) {
   if (!c || !out) return c ? lb_fail(c, LB_EINVAL, "out is null") : LB_EINVAL;
-  int rc = run_diag(c, false);
+  int rc = c->sample_pending ? flush_sample(c) : run_diag(c, false);
   if (rc) return rc;
   double h[5];
   LB_CU(c, cudaMemcpyAsync(h, c->diag + c->p.nz + 1, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -463,6 +482,8 @@ int lb_populations(lb_ctx* c, double* f, double* g, int on_device) {
 
 int lb_save(lb_ctx* c, const char* path) {
   if (!c || !path) return c ? lb_fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
+  const int frc = flush_sample(c);    // the saved time average includes every due sample
+  if (frc) return frc;
   const size_t pbytes = (size_t)Q * c->N * c->ops->esize;
   std::vector<unsigned char> buf(2 * pbytes);
   CkptHeader h;
@@ -503,6 +524,7 @@ int lb_load(lb_ctx* c, const char* path) {
   LB_CU(c, cudaMemcpyAsync(c->nu_acc, h.nu_acc, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   LB_CU(c, cudaStreamSynchronize(c->stream));
   c->step = h.step;
+  c->sample_pending = false;
   c->rho0 = h.rho0;
   c->T0 = h.T0;
   return LB_OK;

@@ -24,6 +24,10 @@ struct lb_ctx {
   double* fields = nullptr;  // [5][N] staging for host-bound lb_moments
   double* pops = nullptr;    // [38][N] staging for host-bound lb_populations
   long long step = 0;
+  // the current state is due for a Nu sample (nu_every) that the next step's launch takes in
+  // passing (fused step + diagnostics); lb_nusselt, lb_diagnostics, lb_save and
+  // lb_adjoint_step take it first with a separate moments pass
+  bool sample_pending = false;
   std::string err;
 };
 
@@ -45,3 +49,5 @@ tlbm::KArgs make_args(const lb_ctx* c);
 dim3 fused_grid(const lb_ctx* c);
 int run_diag(lb_ctx* c, bool accumulate);
 int run_diag_acc(lb_ctx* c, double* acc);
+int finalize_diag(lb_ctx* c, double* acc);   // Nu(z) and health values from the partials
+int flush_sample(lb_ctx* c);                 // take a pending Nu sample (moments pass)

@@ -193,7 +193,10 @@ __device__ __forceinline__ void g_wall_fix(R (&g)[Q], const S* __restrict__ fin,
   }
 }
 
-enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
+// MODE_STEP: one time step. MODE_MOMENTS: the moments of the current state (fields and/or the
+// diagnostics partials), no collision. MODE_STEP_DIAG: one time step that also forms the
+// diagnostics partials of the state it reads (the Nu sample of that state, fused).
+enum { MODE_STEP = 0, MODE_MOMENTS = 1, MODE_STEP_DIAG = 2 };
 
 // Reciprocal and exponential per compute precision: IEEE for FP64 (parity form); the rounded
 // MUFU-based forms for FP32 (relative error ~1e-7, far below the FP32 form's tolerance).
@@ -341,6 +344,7 @@ __global__ void __launch_bounds__(BX * BY, MinBlocks<S, BY>::v)
 lb_fused_kernel(const KArgs a) {
   constexpr int FORCE = (VAR & VAR_GUO) ? FORCE_GUO : FORCE_SHIFT;
   constexpr bool VDW = (VAR & VAR_VDW) != 0;
+  constexpr bool COLLIDE = MODE != MODE_MOMENTS, DIAG = MODE != MODE_STEP;
   using R = typename Store<S>::R;
   using GE = Geo<BY>;
   constexpr int NT = GE::NT, RX = GE::RX, RXY = GE::RXY, HX = GE::HX, HXY = GE::HXY;
@@ -457,7 +461,7 @@ lb_fused_kernel(const KArgs a) {
       }
     }
     __syncthreads();
-    if constexpr (MODE == MODE_MOMENTS) {
+    if constexpr (DIAG) {
       // the partials of the plane collided in the previous iteration are complete
       if (a.part != nullptr && p - 3 >= z0 && p - 3 < z1) moments_combine<R, BY>(a, p - 3, tile, tid);
     }
@@ -542,7 +546,23 @@ lb_fused_kernel(const KArgs a) {
       const R T = E * inv;
       const R* u0 = u_s + slot3(z) * 3 * HXY;
       const R ux = u0[cc], uy = u0[HXY + cc], uz = u0[2 * HXY + cc];
-      if constexpr (MODE == MODE_STEP) {
+      if constexpr (DIAG) {
+        // U = c_v T + int_0^rho P_NI/s^2 ds: (G/4) e^{-2/rho}, or -T_v ln(1 - b rho) - a rho (vdW)
+        if constexpr (sizeof(R) == 8) {
+          const double U = a.c_v * T + (VDW ? -kp.vT * log(1.0 - kp.vb * rho) - kp.va * rho
+                                            : 0.25 * a.G * exp(-2.0 / rho));
+          d_conv = rho * U * uz;
+        } else {
+          // FP32-compute forms: the node's term in float (relative error ~1e-7, far inside these
+          // forms' tolerance; on GB300 FP64 instructions cost more than the step itself)
+          const R U = R(a.c_v) * T + (VDW ? -kp.vT * logf(R(1) - kp.vb * rho) - kp.va * rho
+                                          : R(0.25) * G * fexp(R(-2) * inv));
+          d_conv = rho * U * uz;
+        }
+        d_T = T; d_rho = rho; d_E = E; d_mr = rho; d_mT = T;
+        d_bad = !(isfinite(rho) && isfinite(T) && isfinite(ux) && isfinite(uy) && isfinite(uz));
+      }
+      if constexpr (COLLIDE) {
         const R* Fs = F_s + slot2(z) * 3 * TXY;
         const R Fx = Fs[t], Fy = Fs[TXY + t], Fz = Fs[2 * TXY + t];
         const R* um = u_s + slot3(z - 1) * 3 * HXY;
@@ -620,23 +640,9 @@ lb_fused_kernel(const KArgs a) {
         if (a.uy_out) a.uy_out[own] = double(uy);
         if (a.uz_out) a.uz_out[own] = double(uz);
         if (a.T_out) a.T_out[own] = double(T);
-        // U = c_v T + int_0^rho P_NI/s^2 ds: (G/4) e^{-2/rho}, or -T_v ln(1 - b rho) - a rho (vdW)
-        if constexpr (sizeof(R) == 8) {
-          const double U = a.c_v * T + (VDW ? -kp.vT * log(1.0 - kp.vb * rho) - kp.va * rho
-                                            : 0.25 * a.G * exp(-2.0 / rho));
-          d_conv = rho * U * uz;
-        } else {
-          // FP32-compute forms: the node's term in float (relative error ~1e-7, far inside these
-          // forms' tolerance; on GB300 FP64 instructions cost more than the step itself)
-          const R U = R(a.c_v) * T + (VDW ? -kp.vT * logf(R(1) - kp.vb * rho) - kp.va * rho
-                                          : R(0.25) * G * fexp(R(-2) * inv));
-          d_conv = rho * U * uz;
-        }
-        d_T = T; d_rho = rho; d_E = E; d_mr = rho; d_mT = T;
-        d_bad = !(isfinite(rho) && isfinite(T) && isfinite(ux) && isfinite(uy) && isfinite(uz));
       }
     }
-    if constexpr (MODE == MODE_MOMENTS) {
+    if constexpr (DIAG) {
       if (a.part != nullptr && cplane) {
         // warp-shuffle reduction of the plane partials in the compute precision (the
         // non-finite count by ballot); combined over the warps in FP64 after the next barrier
@@ -655,7 +661,7 @@ lb_fused_kernel(const KArgs a) {
     // (and f-cache) slot that this C stage read.
     if (D == 3) __syncthreads();
   }
-  if constexpr (MODE == MODE_MOMENTS) {
+  if constexpr (DIAG) {
     // the chunk's last plane
     if (a.part != nullptr) {
       __syncthreads();

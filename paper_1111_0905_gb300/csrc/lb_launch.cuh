@@ -42,6 +42,7 @@ template <class S> struct OpsImpl {
     if ((e = attr<BY, MODE_STEP, VAR_GUO>()) != cudaSuccess) return e;
     if ((e = attr<BY, MODE_STEP, VAR_VDW>()) != cudaSuccess) return e;
     if ((e = attr<BY, MODE_STEP, VAR_GUO | VAR_VDW>()) != cudaSuccess) return e;
+    if ((e = attr<BY, MODE_STEP_DIAG, 0>()) != cudaSuccess) return e;
     if ((e = attr<BY, MODE_MOMENTS, 0>()) != cudaSuccess) return e;
     return attr<BY, MODE_MOMENTS, VAR_VDW>();
   }
@@ -93,6 +94,8 @@ template <class S> struct OpsImpl {
   }
   template <int BY> static cudaError_t go_by(const KArgs& a, int mode, dim3 grid, cudaStream_t st) {
     const int var = variant_of(a.forcing, a.psi_kind);
+    // the fused step + Nu sample exists for the paper's scheme only (the caller checks)
+    if (mode == MODE_STEP_DIAG) return var == 0 ? go<BY, MODE_STEP_DIAG, 0>(a, grid, st) : cudaErrorInvalidValue;
     if (mode == MODE_STEP) {
       switch (var) {
         case 0: return go<BY, MODE_STEP, 0>(a, grid, st);

@@ -375,3 +375,30 @@ def test_variant_arguments(lblib, cuda):
         lat.adjoint(4, 2)
     assert e.value.code == -6
     lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(lb.LB_FP64, 1e-12), (lb.LB_FP32, 1e-6), (lb.LB_FP16_DEV, 1e-6)])
+def test_fused_nu_samples_equal_separate_passes(lblib, cuda, prec, tol):
+    """With nu_every the Nu sample of state n is taken by the launch of step n -> n+1 (fused); the
+    time average equals the mean of lb_nusselt called after every step (separate moments
+    passes), and a checkpoint taken mid-run carries the samples due so far."""
+    w = config.boiling_cell(20, nz=14, ny=9, precision=prec)
+    rho, T = w.fields()
+    p = w.params
+    p.nu_every = 1
+    a = lb.Lattice(p, rho, T)
+    a.step(7)
+    q = lb.Params(**{**p.__dict__, "nu_every": 0})
+    b = lb.Lattice(q, rho, T)
+    samples = []
+    for _ in range(7):
+        b.step(1)
+        samples.append(b.nusselt()[0])
+    avg = a.nusselt()[2]
+    assert abs(avg - np.mean(samples)) <= tol * abs(np.mean(samples)), (avg, np.mean(samples))
+    a.step(5)
+    for _ in range(5):
+        b.step(1)
+        samples.append(b.nusselt()[0])
+    assert abs(a.nusselt()[2] - np.mean(samples)) <= tol * abs(np.mean(samples))
+    a.close(); b.close()
