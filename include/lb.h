@@ -135,9 +135,12 @@ int lb_nusselt(lb_ctx* ctx, double* nu_mean, double* nu_z, double* nu_time_avg);
  * operations of lb_step (streaming and wall rules, f and g collisions with the counter term, the
  * velocities and divergence, the force of Eq. (9) with psi = exp(-1/rho), the moments of Eq. (8))
  * in FP64 around the forward states of the context's precision, which are recomputed segment by
- * segment from checkpoints taken every checkpoint_every steps. Output pointers may be NULL.
- * Device memory: nsteps/checkpoint_every + 1 population checkpoints, checkpoint_every + 1 float64
- * states, 2 float64 adjoint states and ~35 float64 fields, allocated and freed by the call.
+ * segment from checkpoints taken every checkpoint_every steps (with FP64 storage the recomputing
+ * step writes the fields the reverse sweep needs; the last segment's come from the forward
+ * sweep). J is accumulated in the reverse sweep from the identity Nu_mean = 1 + sum_x rho U u_z /
+ * (kappa (T_d - T_u) nx ny) (the conduction term telescopes). Output pointers may be NULL.
+ * Device memory: nsteps/checkpoint_every + 1 population checkpoints, checkpoint_every + 1 sets of
+ * 20 float64 fields, 3 float64 states and 15 float64 fields, allocated and freed by the call.
  * Synchronises. Errors: LB_EINVAL (nsteps < 1, checkpoint_every < 1, T_d == T_u, dJ_dT0 requested
  * after lb_step), LB_EUNSUP (a scheme variant: the reverse pass transposes the paper's scheme
  * only), LB_ENOMEM, LB_ECUDA. */

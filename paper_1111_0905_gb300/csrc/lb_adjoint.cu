@@ -30,14 +30,12 @@ struct Par {
   int include_nu;   // add (1/N_t) dNu_mean/dx of this state
 };
 
-// fields of M (recomputed forward macros of one state), each [N]
-enum { MF_RHO = 0, MF_JX, MF_JY, MF_JZ, MF_E, MF_T, MF_PSI, MF_FX, MF_FY, MF_FZ, MF_UX, MF_UY, MF_UZ,
-       MF_VX, MF_VY, MF_VZ, MF_D, MF_AX, MF_AY, MF_AZ, MF_COUNT };
+// fields of M (forward macros of one state, MF_* of lb_kernels.cuh), each [N]
 // fields of A (adjoints of the macros), each [N]
 enum { AF_RHO = 0, AF_T, AF_UX, AF_UY, AF_UZ, AF_VX, AF_VY, AF_VZ, AF_D, AF_FX, AF_FY, AF_FZ, AF_JX, AF_JY,
        AF_JZ, AF_COUNT };
 // per-block parameter partials
-enum { P_TD = 0, P_TU, P_G, P_COUNT };
+enum { P_TD = 0, P_TU, P_G, P_J, P_COUNT };
 
 constexpr int kBlocks = 1024;
 constexpr int kThreads = 256;
@@ -123,13 +121,32 @@ __global__ void div_fwd_kernel(Geom g, double* __restrict__ M) {
 }
 
 // streaming^T, wall rules^T, collision^T and the Nu terms, per node
-__global__ void coll_adj_kernel(const double* __restrict__ X, const double* __restrict__ M,
-                                const double* __restrict__ Ln, Geom g, Par p,
-                                double* __restrict__ L, double* __restrict__ A,
-                                double* __restrict__ part) {
+// adjoint of post-collision population l at node (x, y, z): lambda'_l(x + c_l), or through a wall
+// the bounce-back that delivered f*_l(x) as f'_{opp(l)}(x) (g: with a minus sign)
+__device__ __forceinline__ void adj_pull(const double* __restrict__ Ln, const Geom& g, int l, int i,
+                                         int x, int y, int z, double& lf, double& lg) {
+  const size_t N = g.N;
+  const int zn = z + CZ(l);
+  if (zn < 0 || zn >= g.nz) {
+    lf = Ln[OPP(l) * N + i];
+    lg = -Ln[(Q + OPP(l)) * N + i];
+  } else {
+    const int j = at(g, x + CX(l), y + CY(l), zn);
+    lf = Ln[l * N + j];
+    lg = Ln[(Q + l) * N + j];
+  }
+}
+
+// collision^T, one node per thread. The populations are taken in pairs (l, opp(l)), whose
+// equilibria share the part even in c_l and differ in sign in the odd part: with s = a_l + a_opp
+// and d = a_l - a_opp the pair contributes s (even part) + d (odd part) to each adjoint.
+__global__ void __launch_bounds__(256) coll_adj_kernel(const double* __restrict__ X, const double* __restrict__ M,
+                                                       const double* __restrict__ Ln, Geom g, Par p,
+                                                       double* __restrict__ L, double* __restrict__ A,
+                                                       double* __restrict__ part) {
   __shared__ double sh[32];
   const size_t N = g.N;
-  double pTd = 0.0, pTu = 0.0, pG = 0.0;
+  double pTd = 0.0, pTu = 0.0, pG = 0.0, pJ = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
     int x, y, z;
     coords(i, g, x, y, z);
@@ -137,23 +154,8 @@ __global__ void coll_adj_kernel(const double* __restrict__ X, const double* __re
     const double ux = M[MF_UX * N + i], uy = M[MF_UY * N + i], uz = M[MF_UZ * N + i];
     const double vx = M[MF_VX * N + i], vy = M[MF_VY * N + i], vz = M[MF_VZ * N + i];
     const double D = M[MF_D * N + i];
-    // adjoint of the post-collision populations: lambda*_l(x) = lambda'_l(x + c_l), or through a
-    // wall: the bounce-back that delivered f*_l(x) as f'_{opp(l)}(x) (g: with a minus sign)
-    double lf[Q], lg[Q];
     double a_rho = 0.0;
     if (Ln) {
-#pragma unroll
-      for (int l = 0; l < Q; ++l) {
-        const int zn = z + CZ(l);
-        if (zn < 0 || zn >= g.nz) {
-          lf[l] = Ln[OPP(l) * N + i];
-          lg[l] = -Ln[(Q + OPP(l)) * N + i];
-        } else {
-          const int j = at(g, x + CX(l), y + CY(l), zn);
-          lf[l] = Ln[l * N + j];
-          lg[l] = Ln[(Q + l) * N + j];
-        }
-      }
       // thermal wall rule: g'_m(x_w) = ... + 2 w_m [rho T_w + 4.5 (lam T_w - rho T_w/3)(|c_m|^2-1)]
 #pragma unroll
       for (int m = 0; m < Q; ++m) {
@@ -167,39 +169,53 @@ __global__ void coll_adj_kernel(const double* __restrict__ X, const double* __re
           if (bot) pTd += dTw; else pTu += dTw;
         }
       }
-    } else {
-#pragma unroll
-      for (int l = 0; l < Q; ++l) { lf[l] = 0.0; lg[l] = 0.0; }
     }
     // collision^T: f* = (1 - om) f + om f^eq(rho, v, T), g* = (1 - omk) g + omk g^eq(rho, T, u) + w S
-    double a_T = 0.0, a_v[3] = {0.0, 0.0, 0.0}, a_u[3] = {0.0, 0.0, 0.0};
     const double vv = vx * vx + vy * vy + vz * vz, uu = ux * ux + uy * uy + uz * uz;
-    double lS = 0.0;
+    double a_T = 0.0, lS = 0.0;
+    double sfk = 0.0, sf = 0.0, sg = 0.0;          // sums of s_f k, s_f and s_g over the pairs
+    double avx = 0.0, avy = 0.0, avz = 0.0, aux = 0.0, auy = 0.0, auz = 0.0;
+    const double Tm = 4.5 * (T - 1.0 / 3.0), lk = 4.5 * (p.lam - rho / 3.0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
+      if (l != 0 && (l & 1) == 0) continue;    // with its odd partner
+      const int o = (l == 0) ? 0 : OPP(l);
+      double lf = 0.0, lg = 0.0, lfo = 0.0, lgo = 0.0;
+      if (Ln) {
+        adj_pull(Ln, g, l, i, x, y, z, lf, lg);
+        if (l != 0) adj_pull(Ln, g, o, i, x, y, z, lfo, lgo);
+      }
+      L[l * N + i] = (1.0 - p.om) * lf;
+      L[(Q + l) * N + i] = (1.0 - p.omk) * lg;
+      if (l != 0) {
+        L[o * N + i] = (1.0 - p.om) * lfo;
+        L[(Q + o) * N + i] = (1.0 - p.omk) * lgo;
+      }
       const double k = CSQ(l) - 1, w = WT<double>(l);
       const double cv = CX(l) * vx + CY(l) * vy + CZ(l) * vz;
-      const double Qf = 1.0 + 3.0 * cv + 4.5 * cv * cv - 1.5 * vv + 4.5 * (T - 1.0 / 3.0) * k;
-      const double af = p.om * lf[l] * w;
-      a_rho += af * Qf;
-      a_T += af * rho * 4.5 * k;
-      const double dv = af * rho;
-      a_v[0] += dv * (3.0 * CX(l) + 9.0 * cv * CX(l) - 3.0 * vx);
-      a_v[1] += dv * (3.0 * CY(l) + 9.0 * cv * CY(l) - 3.0 * vy);
-      a_v[2] += dv * (3.0 * CZ(l) + 9.0 * cv * CZ(l) - 3.0 * vz);
       const double cu = CX(l) * ux + CY(l) * uy + CZ(l) * uz;
-      const double Pu = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu;
-      const double ag = p.omk * lg[l] * w;
-      a_rho += ag * T * (Pu - 1.5 * k);
-      a_T += ag * (rho * Pu + 4.5 * (p.lam - rho / 3.0) * k);
-      const double du = ag * E;
-      a_u[0] += du * (3.0 * CX(l) + 9.0 * cu * CX(l) - 3.0 * ux);
-      a_u[1] += du * (3.0 * CY(l) + 9.0 * cu * CY(l) - 3.0 * uy);
-      a_u[2] += du * (3.0 * CZ(l) + 9.0 * cu * CZ(l) - 3.0 * uz);
-      lS += w * lg[l];
-      L[l * N + i] = (1.0 - p.om) * lf[l];
-      L[(Q + l) * N + i] = (1.0 - p.omk) * lg[l];
+      const double af = p.om * w * lf, afo = p.om * w * lfo;
+      const double ag = p.omk * w * lg, ago = p.omk * w * lgo;
+      const double s_f = af + afo, d_f = af - afo, s_g = ag + ago, d_g = ag - ago;
+      // f^eq: even 1 + 4.5 (c.v)^2 - 1.5 v.v + 4.5 (T - 1/3) k, odd 3 c.v; d/dT 4.5 k rho;
+      // d/dv rho (3 c + 9 (c.v) c - 3 v)
+      a_rho += s_f * (1.0 + 4.5 * cv * cv - 1.5 * vv + Tm * k) + d_f * (3.0 * cv);
+      sfk += s_f * k;
+      sf += s_f;
+      const double ef = 3.0 * d_f + 9.0 * s_f * cv;
+      avx += ef * CX(l); avy += ef * CY(l); avz += ef * CZ(l);
+      // g^eq: rho T P(u) + 4.5 (lam T - rho T/3) k, P even 1 + 4.5 (c.u)^2 - 1.5 u.u, odd 3 c.u
+      const double Pe = 1.0 + 4.5 * cu * cu - 1.5 * uu, Po = 3.0 * cu;
+      a_rho += T * (s_g * (Pe - 1.5 * k) + d_g * Po);
+      a_T += rho * (s_g * Pe + d_g * Po) + s_g * lk * k;
+      sg += s_g;
+      const double eg = 3.0 * d_g + 9.0 * s_g * cu;
+      aux += eg * CX(l); auy += eg * CY(l); auz += eg * CZ(l);
+      lS += w * (lg + lgo);
     }
+    a_T += 4.5 * rho * sfk;
+    double a_v[3] = {rho * (avx - 3.0 * vx * sf), rho * (avy - 3.0 * vy * sf), rho * (avz - 3.0 * vz * sf)};
+    double a_u[3] = {E * (aux - 3.0 * ux * sg), E * (auy - 3.0 * uy * sg), E * (auz - 3.0 * uz * sg)};
     // counter term S = -rho T D / c_v
     a_rho += lS * (-T * D / p.cv);
     a_T += lS * (-rho * D / p.cv);
@@ -212,6 +228,7 @@ __global__ void coll_adj_kernel(const double* __restrict__ X, const double* __re
       a_T += p.Kc * rho * p.cv * uz;
       a_u[2] += p.Kc * rho * U;
       pG += p.Kc * rho * uz * 0.25 * e2;
+      pJ += p.Kc * rho * U * uz;       // J = 1 + sum_n sum_x Kc rho U u_z (conduction telescopes)
       const double conv = p.Kc * rho * U * uz / (p.Td - p.Tu);
       pTd -= conv;
       pTu += conv;
@@ -221,10 +238,12 @@ __global__ void coll_adj_kernel(const double* __restrict__ X, const double* __re
     A[AF_VX * N + i] = a_v[0]; A[AF_VY * N + i] = a_v[1]; A[AF_VZ * N + i] = a_v[2];
   }
   const double s0 = block_sum(pTd, sh), s1 = block_sum(pTu, sh), s2 = block_sum(pG, sh);
+  const double s3 = block_sum(pJ, sh);
   if (threadIdx.x == 0) {
     part[blockIdx.x * P_COUNT + P_TD] += s0;
     part[blockIdx.x * P_COUNT + P_TU] += s1;
     part[blockIdx.x * P_COUNT + P_G] += s2;
+    part[blockIdx.x * P_COUNT + P_J] += s3;
   }
 }
 
@@ -300,12 +319,11 @@ __global__ void force_adj_kernel(const double* __restrict__ M, Geom g, Par p,
 }
 
 // dJ/dT0 from lambda_0: x_0 = (f^eq(rho0, 0, T0), g^eq(rho0, T0, 0))
-__global__ void init_grad_kernel(const double* __restrict__ L0, const double* __restrict__ X0, Geom g,
+__global__ void init_grad_kernel(const double* __restrict__ L0, const double* __restrict__ M0, Geom g,
                                  double lam, double* __restrict__ out) {
   const size_t N = g.N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
-    double rho = 0.0;
-    for (int l = 0; l < Q; ++l) rho += X0[l * N + i];
+    const double rho = M0[MF_RHO * N + i];
     double s = 0.0;
     for (int l = 0; l < Q; ++l) {
       const double k = CSQ(l) - 1, w = WT<double>(l);
@@ -346,33 +364,50 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
   cudaStream_t st = c->stream;
   Geom g{c->p.nx, c->p.ny, c->p.nz, c->plane, c->N};
 
-  DevBuf ck, rb, xs, mb, ab, lb, pt, acc, d0;
+  // FP64 storage: the step writes the fields of the state it reads (adj_m), so the reverse sweep
+  // needs no separate moments, force and divergence passes; other storage recomputes them in
+  // FP64 from the FP64 image of each state.
+  const bool fields = (c->ops->esize == sizeof(double));
+  const size_t mstate = (size_t)MF_COUNT * N;   // doubles per state's fields
+  DevBuf ck, rb, xs, mb, ab, lb, pt, d0;
   if (cudaMalloc(&ck.p, (size_t)nck * 2 * pbytes) != cudaSuccess ||
       cudaMalloc(&rb.p, 4 * pbytes + 64) != cudaSuccess ||
-      cudaMalloc(&xs.p, (size_t)(K + 1) * sbytes) != cudaSuccess ||
-      cudaMalloc(&mb.p, (size_t)MF_COUNT * N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&xs.p, sbytes) != cudaSuccess ||
+      cudaMalloc(&mb.p, (size_t)(K + 1) * mstate * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&ab.p, (size_t)AF_COUNT * N * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&lb.p, 2 * sbytes) != cudaSuccess ||
       cudaMalloc(&pt.p, (size_t)kBlocks * P_COUNT * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&acc.p, 2 * sizeof(double)) != cudaSuccess ||
       (dJ_dT0 && cudaMalloc(&d0.p, N * sizeof(double)) != cudaSuccess))
     return lb_fail(c, LB_ENOMEM, "adjoint buffers");
   unsigned char* ckp = static_cast<unsigned char*>(ck.p);
   unsigned char* rbp = static_cast<unsigned char*>(rb.p);
-  double* Xs = static_cast<double*>(xs.p);
-  double* M = static_cast<double*>(mb.p);
+  double* X = static_cast<double*>(xs.p);        // FP64 image of one state
+  double* Ms = static_cast<double*>(mb.p);       // fields of the segment's states n0..n1
   double* A = static_cast<double*>(ab.p);
   double* Lb[2] = {static_cast<double*>(lb.p), static_cast<double*>(lb.p) + 2 * Q * N};
   double* part = static_cast<double*>(pt.p);
-  double* jacc = static_cast<double*>(acc.p);
   LB_CU(c, cudaMemsetAsync(part, 0, (size_t)kBlocks * P_COUNT * sizeof(double), st));
-  LB_CU(c, cudaMemsetAsync(jacc, 0, 2 * sizeof(double), st));
   const int frc = flush_sample(c);    // a Nu sample due for the time average of lb_nusselt
   if (frc) return frc;
 
-  // forward: checkpoints every K steps, J from the Nu of states 1..N (the sample of state n is
-  // taken by the launch of step n -> n+1; the last state's by a moments pass)
+  const double dT = c->p.T_d - c->p.T_u;
+  Par par{c->p.tau_nu, 1.0 / c->p.tau_nu, 1.0 / c->p.tau_kappa, c->p.G, c->p.g_z, c->lam, c->p.c_v,
+          c->p.kappa, c->p.T_d, c->p.T_u,
+          1.0 / ((double)nsteps * c->p.kappa * dT * (double)c->p.nx * (double)c->p.ny), 0};
+  const int nb = (int)std::min<long long>(kBlocks, ((long long)N + kThreads - 1) / kThreads);
+  // fields of a state from its storage image (a.fin, a.gin) by the separate FP64 passes
+  auto fields_by_passes = [&](const KArgs& a, double* Mn) -> int {
+    LB_CU(c, c->ops->pops(a, X, X + Q * N, st));
+    macro_kernel<<<nb, kThreads, 0, st>>>(X, g, Mn);
+    force_fwd_kernel<<<nb, kThreads, 0, st>>>(g, par, Mn);
+    div_fwd_kernel<<<nb, kThreads, 0, st>>>(g, Mn);
+    LB_CU(c, cudaGetLastError());
+    return LB_OK;
+  };
+
+  // forward: checkpoints every K steps; with FP64 storage the last segment's fields as it goes
   const dim3 grid = fused_grid(c);
+  const long long n0_last = (nck - 1) * K;
   for (long long n = 0; n < nsteps; ++n) {
     if (n % K == 0) {
       unsigned char* dst = ckp + (size_t)(n / K) * 2 * pbytes;
@@ -380,79 +415,70 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
       LB_CU(c, cudaMemcpyAsync(dst + pbytes, c->g[c->cur], pbytes, cudaMemcpyDeviceToDevice, st));
     }
     KArgs a = make_args(c);
-    if (n >= 1) {
-      a.part = c->part;
-      LB_CU(c, c->ops->fused(a, MODE_STEP_DIAG, c->by, grid, st));
-      const int rc = finalize_diag(c, jacc);
-      if (rc != LB_OK) return rc;
-    } else {
-      LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, st));
-    }
+    if (fields && n >= n0_last) a.adj_m = Ms + (size_t)(n - n0_last) * mstate;
+    LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, st));
     c->cur ^= 1;
     c->step += 1;
   }
-  {
-    const int rc = run_diag_acc(c, jacc);
+  if (fields) {
+    const int rc = fields_by_passes(make_args(c), Ms + (size_t)(nsteps - n0_last) * mstate);
     if (rc != LB_OK) return rc;
   }
 
-  const double dT = c->p.T_d - c->p.T_u;
-  Par par{c->p.tau_nu, 1.0 / c->p.tau_nu, 1.0 / c->p.tau_kappa, c->p.G, c->p.g_z, c->lam, c->p.c_v,
-          c->p.kappa, c->p.T_d, c->p.T_u,
-          1.0 / ((double)nsteps * c->p.kappa * dT * (double)c->p.nx * (double)c->p.ny), 0};
-  const int nb = (int)std::min<long long>(kBlocks, ((long long)N + kThreads - 1) / kThreads);
   int li = 0;   // Lb[li] = lambda_{n+1} (zero before the last state)
   bool have_next = false;
   for (long long s = nck - 1; s >= 0; --s) {
     const long long n0 = s * K;
     const long long n1 = (s == nck - 1) ? nsteps : (s + 1) * K - 1;   // states n0..n1 of this segment
-    // restore the checkpoint into the recompute lattices and store the states as float64
-    unsigned char* src = ckp + (size_t)s * 2 * pbytes;
-    LB_CU(c, cudaMemcpyAsync(rbp, src, pbytes, cudaMemcpyDeviceToDevice, st));
-    LB_CU(c, cudaMemcpyAsync(rbp + pbytes, src + pbytes, pbytes, cudaMemcpyDeviceToDevice, st));
-    int rc = 0;
-    for (long long n = n0; n <= n1; ++n) {
-      KArgs a = make_args(c);
-      a.fin = rbp + (size_t)rc * 2 * pbytes;
-      a.gin = rbp + (size_t)rc * 2 * pbytes + pbytes;
-      double* Xn = Xs + (size_t)(n - n0) * 2 * Q * N;
-      LB_CU(c, c->ops->pops(a, Xn, Xn + Q * N, st));
-      if (n < n1) {
-        a.fout = rbp + (size_t)(1 - rc) * 2 * pbytes;
-        a.gout = rbp + (size_t)(1 - rc) * 2 * pbytes + pbytes;
-        LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, st));
-        rc ^= 1;
+    if (!(fields && s == nck - 1)) {
+      // recompute the segment from its checkpoint: the fields of states n0..n1
+      unsigned char* src = ckp + (size_t)s * 2 * pbytes;
+      LB_CU(c, cudaMemcpyAsync(rbp, src, pbytes, cudaMemcpyDeviceToDevice, st));
+      LB_CU(c, cudaMemcpyAsync(rbp + pbytes, src + pbytes, pbytes, cudaMemcpyDeviceToDevice, st));
+      int rc = 0;
+      for (long long n = n0; n <= n1; ++n) {
+        KArgs a = make_args(c);
+        a.fin = rbp + (size_t)rc * 2 * pbytes;
+        a.gin = rbp + (size_t)rc * 2 * pbytes + pbytes;
+        double* Mn = Ms + (size_t)(n - n0) * mstate;
+        if (!fields || n == n1) {
+          const int frc2 = fields_by_passes(a, Mn);
+          if (frc2 != LB_OK) return frc2;
+        } else {
+          a.adj_m = Mn;
+        }
+        if (n < n1) {
+          a.fout = rbp + (size_t)(1 - rc) * 2 * pbytes;
+          a.gout = rbp + (size_t)(1 - rc) * 2 * pbytes + pbytes;
+          LB_CU(c, c->ops->fused(a, MODE_STEP, c->by, grid, st));
+          rc ^= 1;
+        }
       }
     }
     for (long long n = n1; n >= n0; --n) {
-      const double* Xn = Xs + (size_t)(n - n0) * 2 * Q * N;
+      const double* Mn = Ms + (size_t)(n - n0) * mstate;
       par.include_nu = (n >= 1) ? 1 : 0;
-      macro_kernel<<<nb, kThreads, 0, st>>>(Xn, g, M);
-      force_fwd_kernel<<<nb, kThreads, 0, st>>>(g, par, M);
-      div_fwd_kernel<<<nb, kThreads, 0, st>>>(g, M);
       double* Lcur = Lb[1 - li];
-      coll_adj_kernel<<<nb, kThreads, 0, st>>>(Xn, M, have_next ? Lb[li] : nullptr, g, par, Lcur, A, part);
-      vel_adj_kernel<<<nb, kThreads, 0, st>>>(M, g, par, A);
-      force_adj_kernel<<<nb, kThreads, 0, st>>>(M, g, par, A, Lcur, part);
+      coll_adj_kernel<<<nb, kThreads, 0, st>>>(nullptr, Mn, have_next ? Lb[li] : nullptr, g, par, Lcur, A, part);
+      vel_adj_kernel<<<nb, kThreads, 0, st>>>(Mn, g, par, A);
+      force_adj_kernel<<<nb, kThreads, 0, st>>>(Mn, g, par, A, Lcur, part);
       LB_CU(c, cudaGetLastError());
       li = 1 - li;
       have_next = true;
     }
     if (s == 0 && dJ_dT0) {
-      init_grad_kernel<<<nb, kThreads, 0, st>>>(Lb[li], Xs, g, c->lam, static_cast<double*>(d0.p));
+      init_grad_kernel<<<nb, kThreads, 0, st>>>(Lb[li], Ms, g, c->lam, static_cast<double*>(d0.p));
       LB_CU(c, cudaGetLastError());
     }
   }
   std::vector<double> hp((size_t)kBlocks * P_COUNT);
-  double hj[2];
   LB_CU(c, cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  LB_CU(c, cudaMemcpyAsync(hj, jacc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (dJ_dT0) LB_CU(c, cudaMemcpyAsync(dJ_dT0, d0.p, N * sizeof(double), cudaMemcpyDeviceToHost, st));
   LB_CU(c, cudaStreamSynchronize(st));
-  double s[P_COUNT] = {0.0, 0.0, 0.0};
+  double s[P_COUNT] = {0.0, 0.0, 0.0, 0.0};
   for (int b = 0; b < kBlocks; ++b)
     for (int k = 0; k < P_COUNT; ++k) s[k] += hp[(size_t)b * P_COUNT + k];
-  if (J) *J = hj[0] / (double)nsteps;
+  if (J) *J = 1.0 + s[P_J];
   if (dJ_dTd) *dJ_dTd = s[P_TD];
   if (dJ_dTu) *dJ_dTu = s[P_TU];
   if (dJ_dG) *dJ_dG = s[P_G];

@@ -106,6 +106,12 @@ __host__ __device__ constexpr int variant_of(int forcing, int psi_kind) {
   return (forcing == FORCE_GUO ? VAR_GUO : 0) | (psi_kind == PSI_VDW ? VAR_VDW : 0);
 }
 
+// Forward fields of one state that the discrete adjoint linearises around, each [N] float64:
+// density, momentum, rho T, T, psi, force, physical and equilibrium velocities, div(u) and the
+// psi-gradient sums A of Eq. (9) (F = -G psi A + rho g_z z).
+enum { MF_RHO = 0, MF_JX, MF_JY, MF_JZ, MF_E, MF_T, MF_PSI, MF_FX, MF_FY, MF_FZ, MF_UX, MF_UY, MF_UZ,
+       MF_VX, MF_VY, MF_VZ, MF_D, MF_AX, MF_AY, MF_AZ, MF_COUNT };
+
 struct KArgs {
   const void* fin; const void* gin;   // post-collision lattices of the previous step
   void* fout; void* gout;             // lattices written by this step
@@ -118,6 +124,7 @@ struct KArgs {
   // moments mode outputs (any may be null)
   double* rho_out; double* ux_out; double* uy_out; double* uz_out; double* T_out;
   double* part;                       // [nz][ntiles][NPART] diagnostics partials (may be null)
+  double* adj_m;                      // FP64 step: MF_* fields of the state read ([MF_COUNT][N]) or null
   KPar<double> pd;                    // the parameters above in double ...
   KPar<float> pf;                     // ... and in float
 };
@@ -229,8 +236,10 @@ template <int BY> struct Geo {
   // R units: psi[D][RXY], rj[D][5][HXY] (rho, 1/rho, jx, jy, jz), u[3][3][HXY], F[2][3][TXY];
   // then either the pulled-f cache of the tile, fc[D][Q][TXY] in storage units S, or (STG) the
   // stage of the collision's pulled f and g, stg[2][Q][TXY] in 4-byte words.
+  // fields of each F-ring plane: F, and for FP64 also the psi sums A (the adjoint's fields)
+  template <class S> static constexpr int fslots() { return sizeof(S) == 8 ? 6 : 3; }
   template <class S> static constexpr size_t r_count() {
-    return (size_t)(depth<S>() * (RXY + 5 * HXY) + 9 * HXY + 6 * TXY);
+    return (size_t)(depth<S>() * (RXY + 5 * HXY) + 9 * HXY + 2 * fslots<S>() * TXY);
   }
   template <class S, class R, bool STG> static constexpr size_t smem_bytes() {
     return sizeof(R) * r_count<S>() +
@@ -356,11 +365,12 @@ lb_fused_kernel(const KArgs a) {
   R* psi_s = reinterpret_cast<R*>(smem_raw);  // [D][RXY]
   R* rj_s = psi_s + D * RXY;                  // [D][5][HXY]  rho, 1/rho, jx, jy, jz
   R* u_s = rj_s + D * 5 * HXY;                // [3][3][HXY]  physical velocity
-  R* F_s = u_s + 9 * HXY;                     // [2][3][TXY]  force on the tile
+  constexpr int NFS = GE::template fslots<S>();
+  R* F_s = u_s + 9 * HXY;                     // [2][NFS][TXY]  force (and FP64: psi sums A) on the tile
   // FP32 stages the collision's pulled f and g asynchronously; FP64 and the 16-bit forms keep
   // the f cache (measured faster for them) and pull g directly.
-  S* fc_s = reinterpret_cast<S*>(F_s + 6 * TXY);                 // [D][Q][TXY] (not STG)
-  uint32_t* stg_s = reinterpret_cast<uint32_t*>(F_s + 6 * TXY);  // [2][Q][TXY] (STG)
+  S* fc_s = reinterpret_cast<S*>(F_s + 2 * NFS * TXY);                 // [D][Q][TXY] (not STG)
+  uint32_t* stg_s = reinterpret_cast<uint32_t*>(F_s + 2 * NFS * TXY);  // [2][Q][TXY] (STG)
 
   const S* __restrict__ fin = static_cast<const S*>(a.fin);
   const S* __restrict__ gin = static_cast<const S*>(a.gin);
@@ -474,7 +484,7 @@ lb_fused_kernel(const KArgs a) {
         const R* pp = psi_s + ring<D>(q + 1) * RXY;
         const R* rj = rj_s + ring<D>(q) * 5 * HXY;
         R* us = u_s + slot3(q) * 3 * HXY;
-        R* Fs = F_s + slot2(q) * 3 * TXY;
+        R* Fs = F_s + slot2(q) * NFS * TXY;
         auto unode = [&](int xr, int yr, bool on_tile) {
           const int c = (yr + 2) * RX + (xr + 2);
           R ax = R(0), ay = R(0), az = R(0);
@@ -496,6 +506,7 @@ lb_fused_kernel(const KArgs a) {
           if (on_tile) {
             const int t = yr * BX + xr;
             Fs[t] = Fx; Fs[TXY + t] = Fy; Fs[2 * TXY + t] = Fz;
+            if constexpr (NFS == 6) { Fs[3 * TXY + t] = ax; Fs[4 * TXY + t] = ay; Fs[5 * TXY + t] = az; }
           }
         };
         unode(tx, ty, true);
@@ -563,7 +574,7 @@ lb_fused_kernel(const KArgs a) {
         d_bad = !(isfinite(rho) && isfinite(T) && isfinite(ux) && isfinite(uy) && isfinite(uz));
       }
       if constexpr (COLLIDE) {
-        const R* Fs = F_s + slot2(z) * 3 * TXY;
+        const R* Fs = F_s + slot2(z) * NFS * TXY;
         const R Fx = Fs[t], Fy = Fs[TXY + t], Fz = Fs[2 * TXY + t];
         const R* um = u_s + slot3(z - 1) * 3 * HXY;
         const R* up = u_s + slot3(z + 1) * 3 * HXY;
@@ -584,6 +595,18 @@ lb_fused_kernel(const KArgs a) {
           const R vx = (FORCE == FORCE_GUO) ? ux : (jx + tau * Fx) * inv;
           const R vy = (FORCE == FORCE_GUO) ? uy : (jy + tau * Fy) * inv;
           const R vz = (FORCE == FORCE_GUO) ? uz : (jz + tau * Fz) * inv;
+          if constexpr (NFS == 6) {
+            // FP64: the fields of the state read, for the discrete adjoint's reverse sweep
+            if (a.adj_m != nullptr) {
+              double* m = a.adj_m + own;
+              const size_t n = (size_t)N;
+              m[MF_RHO * n] = rho; m[MF_T * n] = T;
+              m[MF_PSI * n] = psi_s[ring<GE::template depth<S>()>(z) * RXY + (ty + 2) * RX + (tx + 2)];
+              m[MF_UX * n] = ux; m[MF_UY * n] = uy; m[MF_UZ * n] = uz;
+              m[MF_VX * n] = vx; m[MF_VY * n] = vy; m[MF_VZ * n] = vz; m[MF_D * n] = D;
+              m[MF_AX * n] = Fs[3 * TXY + t]; m[MF_AY * n] = Fs[4 * TXY + t]; m[MF_AZ * n] = Fs[5 * TXY + t];
+            }
+          }
           const R ks = R(1) - R(0.5) * om;
           const R uF = ux * Fx + uy * Fy + uz * Fz;
           const R a0 = drho - R(1.5) * rho * (vx * vx + vy * vy + vz * vz);
