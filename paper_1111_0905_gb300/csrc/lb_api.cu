@@ -19,45 +19,57 @@
 
 namespace tlbm {
 
-// Diagnostics finalisation: per-plane sums over tiles in a fixed order, then Nu(z) of Eq. (4)
-// (normalised by kappa (T_d - T_u)/nz) and global min/sums. out layout:
-// [0, nz) Nu(z); nz: Nu_mean; nz+1: min rho; nz+2: min T; nz+3: non-finite count;
-// nz+4: sum rho; nz+5: sum rho T; [nz+8, 2nz+8) per-plane T sums (scratch).
+// Diagnostics finalisation, in two launches so that the FP64 sums (1/64 of the FP32 rate on
+// GB300) spread over the SMs. Every sum has a fixed assignment of terms to threads and a fixed
+// combination tree, so the result does not depend on timing. out layout:
+// [0, nz) Nu(z) of Eq. (4) (normalised by kappa (T_d - T_u)/nz); nz: Nu_mean; nz+1: min rho;
+// nz+2: min T; nz+3: non-finite count; nz+4: sum rho; nz+5: sum rho T;
+// [nz+8, 8nz+8) per-plane sums over the tiles, [7][nz] (scratch).
 // If acc != null, acc[0] += Nu_mean, acc[1] += 1.
-__global__ void __launch_bounds__(1024) lb_diag_finalize(const double* __restrict__ part, int nz, int ntiles,
-                                                         int nxy, double kappa, double T_d, double T_u,
-                                                         double* __restrict__ out, double* __restrict__ acc) {
-  // One CTA of 1024 threads; every sum has a fixed assignment of terms to lanes and a fixed
-  // combination tree, so the result does not depend on timing.
+
+// 1) one CTA (128 threads) per plane: the plane's 7 partials summed (minima taken) over the tiles
+__global__ void __launch_bounds__(128) lb_diag_planes(const double* __restrict__ part, int nz, int ntiles,
+                                                      double* __restrict__ out) {
+  __shared__ double red[7][4];
+  const int z = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[7] = {0.0, 0.0, 0.0, 0.0, 1e300, 1e300, 0.0};
+  for (int k = threadIdx.x; k < ntiles; k += blockDim.x) {
+    const double* p = part + ((size_t)z * ntiles + k) * NPART;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) v[q] = (q == 4 || q == 5) ? fmin(v[q], p[q]) : v[q] + p[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q) v[q] = (q == 4 || q == 5) ? warp_min(v[q]) : warp_sum(v[q]);
+  if (lane == 0)
+    for (int q = 0; q < 7; ++q) red[q][warp] = v[q];
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    const int q = threadIdx.x;
+    double a = red[q][0];
+    for (int w = 1; w < 4; ++w) a = (q == 4 || q == 5) ? fmin(a, red[q][w]) : a + red[q][w];
+    out[nz + 8 + (size_t)q * nz + z] = a;
+  }
+}
+
+// 2) one CTA: Nu(z) from the plane sums with the wall ghosts, Nu_mean and the global values
+__global__ void __launch_bounds__(1024) lb_diag_finalize(int nz, int nxy, double kappa, double T_d,
+                                                         double T_u, double* __restrict__ out,
+                                                         double* __restrict__ acc) {
   __shared__ double red[6][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  double* sT = out + nz + 8;   // per-plane T sums (scratch after the result slots)
-  // per-plane sums of the convective flux and of T over the tiles: one warp per plane
-  for (int z = warp; z < nz; z += nwarp) {
-    double c = 0.0, t = 0.0;
-    for (int k = lane; k < ntiles; k += 32) {
-      c += part[((size_t)z * ntiles + k) * NPART + 0];
-      t += part[((size_t)z * ntiles + k) * NPART + 1];
-    }
-    c = warp_sum(c);
-    t = warp_sum(t);
-    if (lane == 0) { out[z] = c; sT[z] = t; }
-  }
-  __syncthreads();
+  const double* ps = out + nz + 8;   // [7][nz]: conv, T, rho, rho T, min rho, min T, non-finite
+  const double* sT = ps + nz;
   const double norm = kappa * (T_d - T_u) / nz;
-  double s = 0.0;
+  double s = 0.0, sr = 0.0, sE = 0.0, mr = 1e300, mT = 1e300, bad = 0.0;
   for (int z = threadIdx.x; z < nz; z += blockDim.x) {
     const double Tp = (z + 1 < nz) ? sT[z + 1] : 2.0 * T_u * nxy - sT[nz - 1];
     const double Tm = (z - 1 >= 0) ? sT[z - 1] : 2.0 * T_d * nxy - sT[0];
-    const double flux = (out[z] - kappa * 0.5 * (Tp - Tm)) / nxy;
-    out[z] = flux / norm;
-    s += out[z];
-  }
-  // global sums and minima over every (plane, tile) partial
-  double sr = 0.0, sE = 0.0, mr = 1e300, mT = 1e300, bad = 0.0;
-  for (size_t k = threadIdx.x; k < (size_t)nz * ntiles; k += blockDim.x) {
-    const double* p = part + k * NPART;
-    sr += p[2]; sE += p[3]; mr = fmin(mr, p[4]); mT = fmin(mT, p[5]); bad += p[6];
+    const double flux = (ps[z] - kappa * 0.5 * (Tp - Tm)) / nxy;
+    const double nu = flux / norm;
+    out[z] = nu;
+    s += nu;
+    sr += ps[2 * nz + z]; sE += ps[3 * nz + z];
+    mr = fmin(mr, ps[4 * nz + z]); mT = fmin(mT, ps[5 * nz + z]); bad += ps[6 * nz + z];
   }
   s = warp_sum(s); sr = warp_sum(sr); sE = warp_sum(sE); bad = warp_sum(bad);
   mr = warp_min(mr); mT = warp_min(mT);
@@ -165,8 +177,9 @@ void free_all(lb_ctx* c) {
 // Moments pass into the plane partials, then Nu(z) and the global health values into diag;
 // Nu_mean is added to acc[0] (and 1 to acc[1]) when acc is not null.
 int finalize_diag(lb_ctx* c, double* acc) {
-  lb_diag_finalize<<<1, 1024, 0, c->stream>>>(
-      c->part, c->p.nz, c->ntiles, c->p.nx * c->p.ny, c->p.kappa, c->p.T_d, c->p.T_u, c->diag, acc);
+  lb_diag_planes<<<c->p.nz, 128, 0, c->stream>>>(c->part, c->p.nz, c->ntiles, c->diag);
+  lb_diag_finalize<<<1, 1024, 0, c->stream>>>(c->p.nz, c->p.nx * c->p.ny, c->p.kappa, c->p.T_d,
+                                               c->p.T_u, c->diag, acc);
   LB_CU(c, cudaGetLastError());
   return LB_OK;
 }
@@ -348,18 +361,12 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
     }
   }
   if (cudaMalloc(&c->part, (size_t)p.nz * c->ntiles * NPART * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->diag, (size_t)(2 * p.nz + 8) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->diag, (size_t)(8 * p.nz + 8) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->nu_acc, 2 * sizeof(double)) != cudaSuccess) {
     cudaFree(staging);
     return bail(LB_ENOMEM);
   }
   if (cudaMemsetAsync(c->nu_acc, 0, 2 * sizeof(double), c->stream) != cudaSuccess) { cudaFree(staging); return bail(LB_ECUDA); }
-  if (2 * p.nz * sizeof(double) > 48 * 1024 &&
-      cudaFuncSetAttribute(lb_diag_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(2 * p.nz * sizeof(double))) != cudaSuccess) {
-    cudaFree(staging);
-    return bail(LB_ECUDA);
-  }
   c->cur = 0;
   KArgs a = make_args(c);
   a.fout = c->f[0]; a.gout = c->g[0];
