@@ -293,6 +293,7 @@ def run_ours(args):
     sizes = {} if args.no_sizes else size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws)
     variants = {} if args.no_sizes else variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws)
     diagnostics = diagnostics_cost(lb, torch, max_over_ranks, barrier, results[main_form]["ms_per_step"])
+    adjoint = {} if args.no_sizes else adjoint_cost(lb, torch)
 
     main = results[main_form]
     src_hash = kernel_src_hash()
@@ -316,6 +317,7 @@ def run_ours(args):
                "config": config_dict(w, main_form), "roofline": roofline, "cpu_baseline": cpu,
                "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_summary,
                "forms": results, "sizes": sizes, "variants": variants, "diagnostics": diagnostics,
+               "adjoint": adjoint,
                "kernel_src_hash": src_hash}
         print(json.dumps(out))
     if ws > 1:
@@ -379,6 +381,37 @@ def diagnostics_cost(lb, torch, max_over_ranks, barrier, ms_step: float) -> dict
     lat.close()
     return {"nu_every": 1, "ms_per_step": ms, "ms_per_sample": ms - ms_step,
             "step_only_ms": ms_step}
+
+
+def adjoint_cost(lb, torch) -> dict:
+    """The discrete adjoint on the 64^3 boiling cell (FP64, 1000 steps, checkpoints every 50):
+    wall time of lb_adjoint_step (J and dJ/d(T_d, T_u, G)) against the forward run that computes
+    J (1000 steps with a Nu sample each, then lb_nusselt), both from lb_init's state."""
+    from paper_1111_0905_gb300 import config
+    w = config.boiling_cell(64, kappa=0.15, tau_nu=1.25)
+    p = w.params
+    rho, T = w.fields()
+    N, K = 1000, 50
+    lat = lb.Lattice(p, rho, T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got = lat.adjoint(N, K)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    lat.close()
+    q = lb.Params(**{**p.__dict__, "nu_every": 1})
+    lat = lb.Lattice(q, rho, T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.step(N)
+    J = lat.nusselt()[2]
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    lat.close()
+    return {"workload": "boiling cell 64^3 FP64, 1000 steps, checkpoints every 50",
+            "adjoint_s": t_adj, "forward_s": t_fwd, "ratio": t_adj / t_fwd,
+            "J": got["J"], "J_rel_diff_vs_forward": abs(got["J"] - J) / abs(J),
+            "dJ_dTd": got["T_d"], "dJ_dTu": got["T_u"], "dJ_dG": got["G"]}
 
 
 def variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
