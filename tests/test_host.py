@@ -3,6 +3,7 @@ oracle's EOS, the C-ABI library's exports and the binding's struct layout."""
 import ctypes
 import math
 import subprocess
+import sys
 import textwrap
 from pathlib import Path
 
@@ -98,3 +99,23 @@ def test_init_rejects_invalid_parameters_without_a_gpu(lblib):
         with pytest.raises(lb.LBError) as e:
             lb.Lattice(q, rho, T, stream=None)
         assert e.value.code == -1
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference (the FP64 oracle as the reference arm) prints one JSON line
+    with the benchmark's metric, unit and config, impl = reference, a cpu_baseline and an e2e
+    entry with no host-device bytes."""
+    import json
+    out = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"], capture_output=True, text=True, check=True, cwd=ROOT,
+                         timeout=600).stdout
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
