@@ -402,3 +402,36 @@ def test_fused_nu_samples_equal_separate_passes(lblib, cuda, prec, tol):
         samples.append(b.nusselt()[0])
     assert abs(a.nusselt()[2] - np.mean(samples)) <= tol * abs(np.mean(samples))
     a.close(); b.close()
+
+
+def test_nu_sampling_with_health_checks_and_checkpoints(lblib, cuda, tmp_path):
+    """Nu samples due at a health check or a checkpoint are taken there (not lost or doubled):
+    nu_every = 3 with check_every = 2 over 12 steps averages the samples of states 3, 6, 9, 12;
+    a checkpoint saved at step 5 with nu_every = 1 and resumed gives the same time average as the
+    uninterrupted run, bitwise."""
+    w = config.boiling_cell(16, nz=12, ny=8)
+    rho, T = w.fields()
+    p = w.params
+    q = lb.Params(**{**p.__dict__, "nu_every": 3, "check_every": 2})
+    a = lb.Lattice(q, rho, T)
+    b = lb.Lattice(p, rho, T)
+    samples = []
+    for n in range(1, 13):
+        a.step(1)
+        b.step(1)
+        if n % 3 == 0:
+            samples.append(b.nusselt()[0])
+    assert abs(a.nusselt()[2] - np.mean(samples)) <= 1e-12 * abs(np.mean(samples))
+    a.close(); b.close()
+    r = lb.Params(**{**p.__dict__, "nu_every": 1})
+    c = lb.Lattice(r, rho, T)
+    c.step(5)
+    c.save(tmp_path / "nu.bin")
+    c.step(5)
+    full = c.nusselt()[2]
+    c.close()
+    d = lb.Lattice(r, rho, T)
+    d.load(tmp_path / "nu.bin")
+    d.step(5)
+    assert d.nusselt()[2] == full
+    d.close()
