@@ -352,7 +352,8 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   c->rho0 = p.rho0 > 0 ? p.rho0 : sr / N;
   c->T0 = p.T0 > 0 ? p.T0 : sT / N;
 
-  // 64 bytes of padding: the staged 16-bit pulls copy the 4-byte word containing an element
+  // 64 bytes of padding: a word-wide copy of a 16-bit element (stage_word) reads the 4-byte word
+  // that contains it
   const size_t pbytes = (size_t)Q * N * ops->esize + 64;
   for (int k = 0; k < 2; ++k) {
     if (cudaMalloc(&c->f[k], pbytes) != cudaSuccess || cudaMalloc(&c->g[k], pbytes) != cudaSuccess) {
