@@ -158,6 +158,8 @@ KArgs make_args(const lb_ctx* c) {
     a.fbase[k] = w[k] * c->rho0 * (1.0 + 4.5 * (c->T0 - 1.0 / 3.0) * (k - 1));
     a.gbase[k] = w[k] * (a.E0 + 4.5 * (c->lam * c->T0 - a.E0 / 3.0) * (k - 1));
   }
+  for (int l = 0; l < Q; ++l)
+    a.loff[l] = (unsigned)((long long)l * c->N - (long long)CZ(l) * c->plane);
   return a;
 }
 

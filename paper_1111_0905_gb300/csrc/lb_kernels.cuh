@@ -121,6 +121,7 @@ struct KArgs {
   double tau_nu, omega_nu, omega_kappa, G, g_z, lam, inv_cv, c_v, kappa, T_d, T_u;
   double rho0, T0, E0;                // reference state of the deviations (E0 = rho0 T0)
   double fbase[3], gbase[3];          // f^eq(rho0,0,T0), g^eq(rho0,T0,0) per class: rest, axis, diagonal
+  unsigned loff[19];                  // l N - c_lz plane (mod 2^32): lattice and plane part of a pull
   // moments mode outputs (any may be null)
   double* rho_out; double* ux_out; double* uy_out; double* uz_out; double* T_out;
   double* part;                       // [nz][ntiles][NPART] diagnostics partials (may be null)
@@ -281,6 +282,29 @@ __device__ __forceinline__ void pull_raw(S (&v)[Q], const S* __restrict__ buf, u
   }
 }
 
+// The same with the node given by its element index in the plane pz and the steps to its x/y
+// neighbours (dy[0] to y-1, dy[1] to y+1, dx likewise; the periodic wrap folded in); loff as in
+// KArgs. Used by the 16-bit forms' ring pulls (measured faster there; slower for FP32).
+template <class S, bool WALL>
+__device__ __forceinline__ void pull_rel(S (&v)[Q], const S* __restrict__ buf, unsigned N, int pz, int nz,
+                                         unsigned own, const int (&dy)[2], const int (&dx)[2],
+                                         const unsigned (&loff)[19]) {
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const int cz = CZ(l);
+    if (WALL && ((cz > 0 && pz == 0) || (cz < 0 && pz == nz - 1))) {
+      v[l] = buf[(unsigned)OPP(l) * N + own];
+    } else {
+      unsigned e = own + loff[l];
+      if (CY(l) > 0) e += (unsigned)dy[0];
+      if (CY(l) < 0) e += (unsigned)dy[1];
+      if (CX(l) > 0) e += (unsigned)dx[0];
+      if (CX(l) < 0) e += (unsigned)dx[1];
+      v[l] = buf[e];
+    }
+  }
+}
+
 // Element index of the pulled source of population l at node (col[1], row[1], z) (through a wall,
 // when WALL, the bounce-back source opp(l) of the node itself).
 template <bool WALL>
@@ -354,6 +378,10 @@ lb_fused_kernel(const KArgs a) {
   constexpr int FORCE = (VAR & VAR_GUO) ? FORCE_GUO : FORCE_SHIFT;
   constexpr bool VDW = (VAR & VAR_VDW) != 0;
   constexpr bool COLLIDE = MODE != MODE_MOMENTS, DIAG = MODE != MODE_STEP;
+  // Code shape for the register budget: the paper's forcing takes the unswitched staging loops
+  // and 64-bit store addressing (fewer instructions); the Guo-forcing variants, short of
+  // registers, keep the compact forms (measured: 36-48 against 20 bytes of spills otherwise).
+  constexpr bool LEAN = FORCE != FORCE_GUO;
   using R = typename Store<S>::R;
   using GE = Geo<BY>;
   constexpr int NT = GE::NT, RX = GE::RX, RXY = GE::RXY, HX = GE::HX, HXY = GE::HXY;
@@ -386,8 +414,11 @@ lb_fused_kernel(const KArgs a) {
   const R rho0 = kp.rho0, E0 = kp.E0, T0 = kp.T0;
   const R G = kp.G, gz = kp.g_z, lam = kp.lam, Td = kp.T_d, Tu = kp.T_u;
 
-  // Ring nodes of the M stage owned by this thread: wrapped columns/rows of x-1, x, x+1.
+  // Ring nodes of the M stage owned by this thread: wrapped columns/rows of x-1, x, x+1 (FP32,
+  // FP64), or the node's in-plane index and its steps to the x/y neighbours (16-bit forms).
+  constexpr bool REL = sizeof(S) == 2;
   int mcol[MAXM][3], mrow[MAXM][3];
+  int mown[MAXM], mdy[MAXM][2], mdx[MAXM][2];
   short mh[MAXM], mt[MAXM];   // index in the radius-1 ring / in the tile, or -1
 #pragma unroll
   for (int i = 0; i < MAXM; ++i) {
@@ -399,6 +430,9 @@ lb_fused_kernel(const KArgs a) {
       mcol[i][j] = wrapi(gx - 1 + j, nx);
       mrow[i][j] = wrapi(gy - 1 + j, ny) * nx;
     }
+    mown[i] = mrow[i][1] + mcol[i][1];
+    mdx[i][0] = mcol[i][0] - mcol[i][1]; mdx[i][1] = mcol[i][2] - mcol[i][1];
+    mdy[i][0] = mrow[i][0] - mrow[i][1]; mdy[i][1] = mrow[i][2] - mrow[i][1];
     mh[i] = (k < RXY && rx >= 1 && rx <= BX + 2 && ry >= 1 && ry <= BY + 2) ? (short)((ry - 1) * HX + (rx - 1)) : (short)-1;
     mt[i] = (k < RXY && rx >= 2 && rx < BX + 2 && ry >= 2 && ry < BY + 2) ? (short)((ry - 2) * BX + (rx - 2)) : (short)-1;
   }
@@ -426,12 +460,31 @@ lb_fused_kernel(const KArgs a) {
       // start the copies of the collision's pulled f and g; they complete behind M and U
       if (cplane && cvalid) {
         const int t = ty * BX + tx;
+        if constexpr (LEAN) {
+          // unswitched on the wall test: the interior loop carries no bounce-back selects
+          if (wallz) {
 #pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          const unsigned e = wallz ? pull_index<true>(l, N, z, nz, plane, ccol, crow)
-                                   : pull_index<false>(l, N, z, nz, plane, ccol, crow);
-          stage_word<S>(stg_s + l * TXY + t, fin, e);
-          stage_word<S>(stg_s + (Q + l) * TXY + t, gin, e);
+            for (int l = 0; l < Q; ++l) {
+              const unsigned e = pull_index<true>(l, N, z, nz, plane, ccol, crow);
+              stage_word<S>(stg_s + l * TXY + t, fin, e);
+              stage_word<S>(stg_s + (Q + l) * TXY + t, gin, e);
+            }
+          } else {
+#pragma unroll
+            for (int l = 0; l < Q; ++l) {
+              const unsigned e = pull_index<false>(l, N, z, nz, plane, ccol, crow);
+              stage_word<S>(stg_s + l * TXY + t, fin, e);
+              stage_word<S>(stg_s + (Q + l) * TXY + t, gin, e);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int l = 0; l < Q; ++l) {
+            const unsigned e = wallz ? pull_index<true>(l, N, z, nz, plane, ccol, crow)
+                                     : pull_index<false>(l, N, z, nz, plane, ccol, crow);
+            stage_word<S>(stg_s + l * TXY + t, fin, e);
+            stage_word<S>(stg_s + (Q + l) * TXY + t, gin, e);
+          }
         }
       }
       stage_commit();
@@ -442,13 +495,19 @@ lb_fused_kernel(const KArgs a) {
       const bool wallp = (pz == 0 || pz == nz - 1);
       const bool real = (p == pz);
       const int s3 = ring<D>(p);
+      const unsigned zb = (unsigned)pz * plane;
 #pragma unroll
       for (int i = 0; i < MAXM; ++i) {
         const int k = tid + i * NT;
         if (k < RXY) {
           S fr[Q];
-          if (wallp) pull_raw<S, true>(fr, fin, N, pz, nz, plane, mcol[i], mrow[i]);
-          else pull_raw<S, false>(fr, fin, N, pz, nz, plane, mcol[i], mrow[i]);
+          if constexpr (REL) {
+            if (wallp) pull_rel<S, true>(fr, fin, N, pz, nz, zb + (unsigned)mown[i], mdy[i], mdx[i], a.loff);
+            else pull_rel<S, false>(fr, fin, N, pz, nz, zb + (unsigned)mown[i], mdy[i], mdx[i], a.loff);
+          } else {
+            if (wallp) pull_raw<S, true>(fr, fin, N, pz, nz, plane, mcol[i], mrow[i]);
+            else pull_raw<S, false>(fr, fin, N, pz, nz, plane, mcol[i], mrow[i]);
+          }
           R f[Q];
 #pragma unroll
           for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fr[l]);
@@ -583,8 +642,16 @@ lb_fused_kernel(const KArgs a) {
         R D = R(0.5) * (u0[cc + 1] - u0[cc - 1]);
         D = D + R(0.5) * (u0[HXY + cc + HX] - u0[HXY + cc - HX]);
         D = D + R(0.5) * (uzp - uzm);
-        S* __restrict__ fo = static_cast<S*>(a.fout);
-        S* __restrict__ go = static_cast<S*>(a.gout);
+        // Output element of population l of this node: with LEAN from the node's own address, l N
+        // in 64-bit arithmetic (one multiply-add per store), else the 32-bit element index.
+        constexpr bool P64 = LEAN;
+        S* __restrict__ fo = static_cast<S*>(a.fout) + (P64 ? own : 0u);
+        S* __restrict__ go = static_cast<S*>(a.gout) + (P64 ? own : 0u);
+        const size_t NS = N;
+        auto sidx = [&](int l) -> size_t {
+          if constexpr (P64) return (size_t)l * NS;
+          else return (size_t)((unsigned)l * N + own);
+        };
         // f: BGK towards f^eq(rho, u', T), u' = (j + tau F)/rho. f^eq - fbase per class:
         // w [drho - 1.5 rho v.v + 4.5 (|c|^2-1)(dE - drho/3) + 3 rho c.v + 4.5 rho (c.v)^2]
         // (rho (T - 1/3) - rho0 (T0 - 1/3) = dE - drho/3 since rho T = E).
@@ -624,13 +691,13 @@ lb_fused_kernel(const KArgs a) {
               const R cF = R(CX(l)) * Fx + R(CY(l)) * Fy + R(CZ(l)) * Fz;
               const R ws = WT<R>(l) * ks;
               const R ssym = ws * (R(9) * cv * cF - R(3) * uF), sasym = ws * (R(3) * cF);
-              Store<S>::st(fo + ((unsigned)l * N + own), om1 * f[l] + w * (sym + asym) + (ssym + sasym));
+              Store<S>::st(fo + sidx(l), om1 * f[l] + w * (sym + asym) + (ssym + sasym));
               if (l != 0)
-                Store<S>::st(fo + ((unsigned)OPP(l) * N + own),
+                Store<S>::st(fo + sidx(OPP(l)),
                              om1 * f[OPP(l)] + w * (sym - asym) + (ssym - sasym));
             } else {
-              Store<S>::st(fo + ((unsigned)l * N + own), om1 * f[l] + w * (sym + asym));
-              if (l != 0) Store<S>::st(fo + ((unsigned)OPP(l) * N + own), om1 * f[OPP(l)] + w * (sym - asym));
+              Store<S>::st(fo + sidx(l), om1 * f[l] + w * (sym + asym));
+              if (l != 0) Store<S>::st(fo + sidx(OPP(l)), om1 * f[OPP(l)] + w * (sym - asym));
             }
           }
         }
@@ -652,9 +719,9 @@ lb_fused_kernel(const KArgs a) {
             const R sym = B[CLS(l)] + e45 * cu * cu;
             const R asym = e3 * cu;
             const R src = w * Ssrc;
-            Store<S>::st(go + ((unsigned)l * N + own), omk1 * g[l] + (w * omk) * (sym + asym) + src);
+            Store<S>::st(go + sidx(l), omk1 * g[l] + (w * omk) * (sym + asym) + src);
             if (l != 0)
-              Store<S>::st(go + ((unsigned)OPP(l) * N + own), omk1 * g[OPP(l)] + (w * omk) * (sym - asym) + src);
+              Store<S>::st(go + sidx(OPP(l)), omk1 * g[OPP(l)] + (w * omk) * (sym - asym) + src);
           }
         }
       } else {
