@@ -680,14 +680,14 @@ lb_fused_kernel(const KArgs a) {
           const R th = R(4.5) * (dE - drho * R(1.0 / 3.0));
           const R A[3] = {a0 - th, a0, a0 + th};
           const R r3 = R(3) * rho, r45 = R(4.5) * rho;
+          if constexpr (FORCE == FORCE_GUO) {
 #pragma unroll
-          for (int l = 0; l < Q; ++l) {
-            if (l != 0 && (l & 1) == 0) continue;     // handled with its odd partner
-            const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
-            const R w = WT<R>(l) * om;
-            const R sym = A[CLS(l)] + r45 * cv * cv;
-            const R asym = r3 * cv;
-            if constexpr (FORCE == FORCE_GUO) {
+            for (int l = 0; l < Q; ++l) {
+              if (l != 0 && (l & 1) == 0) continue;     // handled with its odd partner
+              const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
+              const R w = WT<R>(l) * om;
+              const R sym = A[CLS(l)] + r45 * cv * cv;
+              const R asym = r3 * cv;
               const R cF = R(CX(l)) * Fx + R(CY(l)) * Fy + R(CZ(l)) * Fz;
               const R ws = WT<R>(l) * ks;
               const R ssym = ws * (R(9) * cv * cF - R(3) * uF), sasym = ws * (R(3) * cF);
@@ -695,9 +695,21 @@ lb_fused_kernel(const KArgs a) {
               if (l != 0)
                 Store<S>::st(fo + sidx(OPP(l)),
                              om1 * f[OPP(l)] + w * (sym - asym) + (ssym - sasym));
-            } else {
-              Store<S>::st(fo + sidx(l), om1 * f[l] + w * (sym + asym));
-              if (l != 0) Store<S>::st(fo + sidx(OPP(l)), om1 * f[OPP(l)] + w * (sym - asym));
+            }
+          } else {
+            // the relaxation weights folded into the per-class coefficients: the even part
+            // w om (A + 4.5 rho (c.v)^2) = wA + q (c.v)^2, the odd part w om 3 rho (c.v) = s (c.v)
+            const R o0 = WT<R>(0) * om, o1 = WT<R>(1) * om, o2 = WT<R>(7) * om;
+            const R wA[3] = {o0 * A[0], o1 * A[1], o2 * A[2]};
+            const R q[3] = {R(0), o1 * r45, o2 * r45}, sc[3] = {R(0), o1 * r3, o2 * r3};
+            Store<S>::st(fo + sidx(0), om1 * f[0] + wA[0]);
+#pragma unroll
+            for (int l = 1; l < Q; l += 2) {
+              const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
+              const R ev = q[CLS(l)] * (cv * cv) + wA[CLS(l)];
+              const R od = sc[CLS(l)] * cv;
+              Store<S>::st(fo + sidx(l), om1 * f[l] + (ev + od));
+              Store<S>::st(fo + sidx(OPP(l)), om1 * f[OPP(l)] + (ev - od));
             }
           }
         }
@@ -711,17 +723,19 @@ lb_fused_kernel(const KArgs a) {
           const R tg = R(4.5) * (lam * ((dE - T0 * drho) * inv) - dE * R(1.0 / 3.0));
           const R B[3] = {b0 - tg, b0, b0 + tg};
           const R e3 = R(3) * E, e45 = R(4.5) * E;
+          // per class: the even part w omk (B + 4.5 E (c.u)^2) + w S = P + q (c.u)^2, the odd
+          // part w omk 3 E (c.u) = s (c.u)
+          const R k0 = WT<R>(0) * omk, k1 = WT<R>(1) * omk, k2 = WT<R>(7) * omk;
+          const R P[3] = {k0 * B[0] + WT<R>(0) * Ssrc, k1 * B[1] + WT<R>(1) * Ssrc, k2 * B[2] + WT<R>(7) * Ssrc};
+          const R q[3] = {R(0), k1 * e45, k2 * e45}, sc[3] = {R(0), k1 * e3, k2 * e3};
+          Store<S>::st(go + sidx(0), omk1 * g[0] + P[0]);
 #pragma unroll
-          for (int l = 0; l < Q; ++l) {
-            if (l != 0 && (l & 1) == 0) continue;
+          for (int l = 1; l < Q; l += 2) {
             const R cu = R(CX(l)) * ux + R(CY(l)) * uy + R(CZ(l)) * uz;
-            const R w = WT<R>(l);
-            const R sym = B[CLS(l)] + e45 * cu * cu;
-            const R asym = e3 * cu;
-            const R src = w * Ssrc;
-            Store<S>::st(go + sidx(l), omk1 * g[l] + (w * omk) * (sym + asym) + src);
-            if (l != 0)
-              Store<S>::st(go + sidx(OPP(l)), omk1 * g[OPP(l)] + (w * omk) * (sym - asym) + src);
+            const R ev = q[CLS(l)] * (cu * cu) + P[CLS(l)];
+            const R od = sc[CLS(l)] * cu;
+            Store<S>::st(go + sidx(l), omk1 * g[l] + (ev + od));
+            Store<S>::st(go + sidx(OPP(l)), omk1 * g[OPP(l)] + (ev - od));
           }
         }
       } else {
