@@ -138,8 +138,12 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(prec_name: str):
+def workload(prec_name: str, n: int = 128):
+    """The headline 128^3 single-phase cell, or (n > 128, profiling with --only) the
+    paper-geometry boiling cell of the size sweep."""
     from paper_1111_0905_gb300 import config
+    if n > 128:
+        return config.paper_scale_cell(n, precision=FORMS[prec_name])
     return config.single_phase_cell(128, precision=FORMS[prec_name])
 
 
@@ -204,7 +208,7 @@ def run_ours(args):
     clock_summary = None
     form_list = [args.only] if args.only else ["f32", "f64", "bf16dev", "fp16dev"]
     for form in form_list:
-        w = workload(form)
+        w = workload(form, args.n if args.only else 128)
         p = w.params
         if args.only:
             p.nu_every = args.nu_every
@@ -535,6 +539,8 @@ def main():
                     "(no errors, e2e or baselines; for profiling)")
     ap.add_argument("--nu-every", type=int, default=0, help="with --only: sample Nu every n steps "
                     "inside the timed steps (the diagnostics path)")
+    ap.add_argument("--n", type=int, default=128, choices=[128, 256, 512],
+                    help="with --only: cube size (256/512: the boiling cell of the size sweep)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
