@@ -102,8 +102,9 @@ def test_adjoint_of_the_fp32_form_matches_fp64(lblib, cuda):
 
 
 def test_adjoint_boiling_64_over_1000_steps(lblib, cuda):
-    """The 64^3 adjoint configuration: 1000 steps, checkpoints every 50; dJ/d(T_d, T_u, G)
-    against central differences (h = 1e-6) within 1e-4, and the cost against the forward run.
+    """The 64^3 adjoint configuration: 1000 steps, checkpoints every 50; dJ/d(T_d, T_u, G) and
+    two random directions of dJ/dT0 (the initial temperature field) against central differences
+    (h = 1e-6) within 1e-4, and the cost against the forward run.
     tau_nu = 1.25 and kappa = 0.15 (lambda = 0.3 in the g^eq positivity window) keep the
     phase-separating cell bounded for the whole run (tau_nu = 1 breaks down after ~500 steps)."""
     w = config.boiling_cell(64, kappa=0.15, tau_nu=1.25)
@@ -113,7 +114,7 @@ def test_adjoint_boiling_64_over_1000_steps(lblib, cuda):
     lat = lb.Lattice(p, rho, T)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    got = lat.adjoint(N, K)
+    got = lat.adjoint(N, K, grad_T0=True)
     t_adj = time.perf_counter() - t0
     lat.close()
     torch.cuda.synchronize()
@@ -130,6 +131,12 @@ def test_adjoint_boiling_64_over_1000_steps(lblib, cuda):
               - _J_gpu(lb.Params(**{**p.__dict__, k: base - h}), rho, T, N)) / (2 * h)
         print(f"  {k}: adjoint {got[k]:.8e}, central difference {fd:.8e}")
         assert abs(fd - got[k]) <= 1e-4 * max(abs(fd), 1e-3), (k, fd, got[k])
+    for seed in (64, 1000):
+        v = np.random.default_rng(seed).standard_normal(T.shape)
+        fd = (_J_gpu(p, rho, T + h * v, N) - _J_gpu(p, rho, T - h * v, N)) / (2 * h)
+        ad = float((got["T0"] * v).sum())
+        print(f"  T0 direction {seed}: adjoint {ad:.8e}, central difference {fd:.8e}")
+        assert abs(fd - ad) <= 1e-4 * max(abs(fd), 1e-3), (seed, fd, ad)
 
 
 @pytest.mark.parametrize("device", ["cpu", "cuda"])
