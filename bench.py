@@ -298,6 +298,7 @@ def run_ours(args):
     variants = {} if args.no_sizes else variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws)
     diagnostics = diagnostics_cost(lb, torch, max_over_ranks, barrier, results[main_form]["ms_per_step"])
     adjoint = {} if args.no_sizes else adjoint_cost(lb, torch)
+    horizons = {} if args.no_sizes else horizon_errors(lb, torch, np)
 
     main = results[main_form]
     src_hash = kernel_src_hash()
@@ -321,7 +322,7 @@ def run_ours(args):
                "config": config_dict(w, main_form), "roofline": roofline, "cpu_baseline": cpu,
                "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_summary,
                "forms": results, "sizes": sizes, "variants": variants, "diagnostics": diagnostics,
-               "adjoint": adjoint,
+               "adjoint": adjoint, "horizon_errors": horizons,
                "kernel_src_hash": src_hash}
         print(json.dumps(out))
     if ws > 1:
@@ -416,6 +417,45 @@ def adjoint_cost(lb, torch) -> dict:
             "adjoint_s": t_adj, "forward_s": t_fwd, "ratio": t_adj / t_fwd,
             "J": got["J"], "J_rel_diff_vs_forward": abs(got["J"] - J) / abs(J),
             "dJ_dTd": got["T_d"], "dJ_dTu": got["T_u"], "dJ_dG": got["G"]}
+
+
+def horizon_errors(lb, torch, np) -> dict:
+    """Errors of the mixed forms against the FP64 step at the stated horizons of the two
+    configurations they are quoted on: the 128^3 single-phase cell after 2000 steps (FP32, BF16,
+    FP16 deviations) and the 256^3 boiling cell after 5000 steps (FP32, BF16, FP16 deviations).
+    Field errors are max |form - FP64| / max |FP64| (u on the largest |u|), with the root mean
+    square of the rho error beside it; Nu_mean of each run and the relative mass change."""
+    from paper_1111_0905_gb300 import config
+    out = {}
+    for name, make, n, steps in (("single_phase_128^3", config.single_phase_cell, 128, 2000),
+                                 ("boiling_256^3", config.paper_scale_cell, 256, 5000)):
+        runs = {}
+        for form in ("f64", "f32", "bf16dev", "fp16dev"):
+            w = make(n, precision=FORMS[form])
+            rho, T = w.fields()
+            lat = lb.Lattice(w.params, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+            m0 = float(lat.diagnostics()["mass"])
+            lat.step(steps)
+            r, u, TT = lat.moments()
+            h = lat.diagnostics()
+            runs[form] = (r, u, TT, lat.nusselt()[0], float(h["mass"]) / m0 - 1.0, int(h["nonfinite"]))
+            lat.close()
+            del rho, T
+            torch.cuda.empty_cache()
+        r64, u64, T64, nu64, dm64, _ = runs["f64"]
+        entry = {"steps": steps, "f64": {"nu_mean": nu64, "mass_change": dm64}}
+        for form in ("f32", "bf16dev", "fp16dev"):
+            r, u, TT, nu, dm, bad = runs[form]
+            entry[form] = {
+                "rho": float(np.abs(r - r64).max() / np.abs(r64).max()),
+                "rho_rms": float(np.sqrt(np.mean((r - r64) ** 2)) / np.abs(r64).max()),
+                "T": float(np.abs(TT - T64).max() / np.abs(T64).max()),
+                "u": float(max(np.abs(u[a] - u64[a]).max() for a in range(3)) /
+                           max(np.abs(u64[a]).max() for a in range(3))),
+                "nu_mean": nu, "nu_rel_err": float(abs(nu - nu64) / abs(nu64)),
+                "mass_change": dm, "nonfinite": bad}
+        out[name] = entry
+    return out
 
 
 def variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
