@@ -511,7 +511,8 @@ def _oracle_sample(side: int):
 
 def cpu_baseline(args) -> dict:
     """FP64 oracle timed on the host cores on a bounded sample of the full 128^3 cell: as many
-    steps as take about 15 s (6 to 100), after one warm-up step."""
+    steps as take about 15 s (6 to 100), after one warm-up step; then on one host thread, as many
+    steps as take about 8 s (1 to 20)."""
     import torch
     from oracle import lbm
     f, g, op = _oracle_sample(128)
