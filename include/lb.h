@@ -50,7 +50,11 @@ typedef enum {
   LB_FP16_DEV = 3  /* float16 storage of the deviations below, float32 compute */
 } lb_precision;
 /* Every precision stores deviations from the reference equilibria, f_l - f^eq_l(rho0, 0, T0) and
- * g_l - g^eq_l(rho0, T0, 0), and forms moments and equilibria from them. */
+ * g_l - g^eq_l(rho0, T0, 0), and forms moments and equilibria from them. The rounding of the
+ * stored deviations is not mass-conserving: measured against the float64 step, float32 stays
+ * within 1e-5 on rho and T over 2000 steps (5e-5 over 5000 boiling steps); float16 within 2e-3
+ * over 2000 single-phase steps but not over long boiling runs; bfloat16 only over short runs
+ * (a few hundred steps). */
 
 /* Scheme variants for comparison with the paper's scheme (variant 0 of each; the paper defines
  * neither alternative). Forcing: LB_FORCE_SHIFT, the paper's equilibrium velocity
