@@ -101,6 +101,34 @@ def test_init_rejects_invalid_parameters_without_a_gpu(lblib):
         assert e.value.code == -1
 
 
+def test_init_rejects_degenerate_and_oversized_grids_without_a_gpu(lblib):
+    """lb_init's own checks, called through the C ABI with small dummy arrays (every check runs
+    before the fields are read or any device call is made): empty grids, grids whose 19 N
+    population offsets overflow 32 bits (the 512^3 workload is inside), the 16-row tile for FP64,
+    negative chunk/sampling/check periods, unknown variants, a van der Waals psi without an
+    attractive coupling, non-positive wall temperatures and a non-finite coupling."""
+    import ctypes
+    import dataclasses
+    import math
+    w = config.boiling_cell(4)
+    p = w.params
+    rho, T = w.fields()
+    cases = [dict(nx=0), dict(ny=0), dict(nz=0), dict(nx=700, ny=700, nz=700),
+             dict(nx=1024, ny=1024, nz=230), dict(precision=lb.LB_FP64, tile_y=16),
+             dict(z_chunk=-1), dict(nu_every=-2), dict(check_every=-1), dict(forcing=2),
+             dict(psi_kind=3), dict(psi_kind=lb.LB_PSI_VDW, G=0.5), dict(T_d=0.0), dict(T_u=-1.0),
+             dict(G=math.inf), dict(c_v=0.0)]
+    for kw in cases:
+        cp = dataclasses.replace(p, **kw).to_c()
+        out = ctypes.c_void_p()
+        rc = lblib.lb_init(ctypes.byref(cp), rho.ctypes.data_as(ctypes.c_void_p),
+                           T.ctypes.data_as(ctypes.c_void_p), 0, None, ctypes.byref(out))
+        assert rc == -1, (kw, rc)
+        assert not out.value
+    # the 512^3 workload itself passes the size checks (19 N < 2^32)
+    assert 19 * 512 ** 3 < 2 ** 32 <= 19 * 700 ** 3
+
+
 def test_reference_arm_prints_the_contract_line():
     """bench.py --impl reference (the FP64 oracle as the reference arm) prints one JSON line
     with the benchmark's metric, unit and config, impl = reference, a cpu_baseline and an e2e
