@@ -4,7 +4,8 @@ Each test checks a property the paper or the mathematics fixes independently of 
 own code: exact mass conservation with halfway walls, momentum conservation of the pair force
 (Eq. (9)) in a periodic box, the gradient limit of Eq. (9), the shear viscosity of Eq. (6),
 the adiabatic sound speed produced by the counter term (Eq. (3), second line), the linear
-conduction profile with the wall temperatures and Nu = 1, and a fixed point at rest.
+conduction profile with the wall temperatures and Nu = 1, the conducted energy flux (the
+magnitude of kappa and the c_v factor), and a fixed point at rest.
 """
 import math
 
@@ -159,3 +160,27 @@ def test_nusselt_of_an_exact_conduction_state_is_one():
     f, g = lbm.init_state(rho, T, p)
     nu_mean, nu_z = lbm.nusselt(f, g, p)
     assert (nu_z - 1).abs().max() < 1e-12
+
+
+@pytest.mark.parametrize("c_v,kappa", [(1.0, 0.1), (2.0, 0.1), (1.0, 0.05)])
+def test_conducted_energy_flux_is_kappa_over_cv_times_the_gradient(c_v, kappa):
+    """The magnitude of the conductivity (which the linear profile and Nu = 1 above do not fix):
+    in the steady conduction state the energy rho T that streaming carries across each interior
+    plane per step, sum of g*_l(z) over c_lz = +1 minus sum of g*_l(z+1) over c_lz = -1, equals
+    kappa (T_d - T_u)/L, the conduction flux of Eq. (3), divided by c_v (the g lattice carries
+    rho T, not rho c_v T), with L = nz between the halfway walls."""
+    nz = 8
+    Td, Tu = 1.05 * TM, 0.95 * TM
+    p = lbm.Params(2, 2, nz, 1.0, 1.0, 0.0, kappa, c_v=c_v, g_z=0.0, T_d=Td, T_u=Tu)
+    z = (torch.arange(nz, dtype=DT) + 0.5) / nz
+    T = (Td + (Tu - Td) * z)[:, None, None].expand(nz, 2, 2).clone()
+    rho = TM / T
+    f, g = lbm.init_state(rho, T, p)
+    f, g = lbm.run(f, g, p, 2000)
+    _, gs, _ = lbm.collide(f, g, p)
+    up = [l for l in range(lbm.Q) if lbm.C[l][2] == 1]
+    down = [l for l in range(lbm.Q) if lbm.C[l][2] == -1]
+    want = kappa / c_v * (Td - Tu) / nz
+    for k in range(nz - 1):
+        q = sum(gs[l, k].mean() for l in up) - sum(gs[l, k + 1].mean() for l in down)
+        assert abs(float(q) / want - 1) < 1e-7, (k, float(q), want)
