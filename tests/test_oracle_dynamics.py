@@ -162,8 +162,9 @@ def test_nusselt_of_an_exact_conduction_state_is_one():
     assert (nu_z - 1).abs().max() < 1e-12
 
 
-@pytest.mark.parametrize("c_v,kappa", [(1.0, 0.1), (2.0, 0.1), (1.0, 0.05)])
-def test_conducted_energy_flux_is_kappa_over_cv_times_the_gradient(c_v, kappa):
+@pytest.mark.parametrize("c_v,kappa,tau_k", [(1.0, 0.1, 1.0), (2.0, 0.1, 1.0), (1.0, 0.05, 1.0),
+                                             (1.0, 0.1, 1.5)])
+def test_conducted_energy_flux_is_kappa_over_cv_times_the_gradient(c_v, kappa, tau_k):
     """The magnitude of the conductivity (which the linear profile and Nu = 1 above do not fix):
     in the steady conduction state the energy rho T that streaming carries across each interior
     plane per step, sum of g*_l(z) over c_lz = +1 minus sum of g*_l(z+1) over c_lz = -1, equals
@@ -171,7 +172,7 @@ def test_conducted_energy_flux_is_kappa_over_cv_times_the_gradient(c_v, kappa):
     rho T, not rho c_v T), with L = nz between the halfway walls."""
     nz = 8
     Td, Tu = 1.05 * TM, 0.95 * TM
-    p = lbm.Params(2, 2, nz, 1.0, 1.0, 0.0, kappa, c_v=c_v, g_z=0.0, T_d=Td, T_u=Tu)
+    p = lbm.Params(2, 2, nz, 1.0, tau_k, 0.0, kappa, c_v=c_v, g_z=0.0, T_d=Td, T_u=Tu)
     z = (torch.arange(nz, dtype=DT) + 0.5) / nz
     T = (Td + (Tu - Td) * z)[:, None, None].expand(nz, 2, 2).clone()
     rho = TM / T
