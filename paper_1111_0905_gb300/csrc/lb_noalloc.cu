@@ -30,7 +30,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// One block per plane z: fixed-order FP64 sums of rho U u_z (U = c_v T + (G/4) e^{-2/rho}) and T.
+// One block per plane z: fixed-order FP64 sums of rho U u_z and T, with the internal energy of
+// the paper's pseudopotential psi = exp(-1/rho), U = c_v T + (G/4) e^{-2/rho} (Eq. (2)).
 __global__ void plane_sums_kernel(const double* __restrict__ rho, const double* __restrict__ uz,
                                   const double* __restrict__ T, int nxy, double c_v, double G,
                                   double* __restrict__ sums) {
@@ -102,10 +103,16 @@ extern "C" int lb_nusselt_fields_noalloc(const double* rho, const double* uz, co
   int rc = scratch_for_current_device(&sums);
   if (rc != LB_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const int nxy = nx * ny;
-  plane_sums_kernel<<<nz, 256, 0, st>>>(rho, uz, T, nxy, c_v, G, sums);
-  if (cudaGetLastError() != cudaSuccess) return LB_ECUDA;
-  finalize_kernel<<<1, 256, 0, st>>>(sums, nz, nxy, kappa, T_d, T_u, nu_out);
-  if (cudaGetLastError() != cudaSuccess) return LB_ECUDA;
+  int nxy = nx * ny;
+  // Launch errors are taken from cudaLaunchKernel's own return value. The runtime's last-error
+  // slot is only peeked at, never cleared: an error that the caller's earlier work left there
+  // stays for the caller, and is not reported as this call's failure.
+  const cudaError_t before = cudaPeekAtLastError();
+  void* a1[] = {(void*)&rho, (void*)&uz, (void*)&T, (void*)&nxy, (void*)&c_v, (void*)&G, (void*)&sums};
+  cudaError_t e = cudaLaunchKernel((const void*)plane_sums_kernel, dim3(nz), dim3(256), a1, 0, st);
+  if (e != cudaSuccess && e != before) return LB_ECUDA;
+  void* a2[] = {(void*)&sums, (void*)&nz, (void*)&nxy, (void*)&kappa, (void*)&T_d, (void*)&T_u, (void*)&nu_out};
+  e = cudaLaunchKernel((const void*)finalize_kernel, dim3(1), dim3(256), a2, 0, st);
+  if (e != cudaSuccess && e != before) return LB_ECUDA;
   return LB_OK;
 }

@@ -42,5 +42,32 @@ def test_noalloc_rejects_sizes_beyond_its_array(lblib, cuda):
     with pytest.raises(lb.LBError) as e:
         lb.nusselt_fields_noalloc(big, x, x, x, x)
     assert e.value.code == -1
-    with pytest.raises(lb.LBError):
-        lb.nusselt_fields_noalloc(p, None, x, x, x)
+    # a null pointer is refused by the entry point itself (the binding refuses it earlier)
+    n = p.nx * p.ny * p.nz
+    f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = torch.zeros(p.nz + 1, dtype=torch.float64, device="cuda")
+    rc = lblib.lb_nusselt_fields_noalloc(None, f.data_ptr(), f.data_ptr(), p.nx, p.ny, p.nz, p.kappa,
+                                         p.G, p.c_v, p.T_d, p.T_u, out.data_ptr(), None)
+    assert rc == -1
+    with pytest.raises(ValueError):
+        lb.nusselt_fields_noalloc(p, None, f, f, out)
+
+
+def test_noalloc_binding_refuses_tensors_the_kernels_would_misread(lblib, cuda):
+    """Wrong dtype, a transposed view, short inputs or a short output never reach the device."""
+    p = config.boiling_cell(8, nz=6, ny=5).params
+    shape = (p.nz, p.ny, p.nx)
+    good = torch.ones(shape, dtype=torch.float64, device="cuda")
+    out = torch.zeros(p.nz + 1, dtype=torch.float64, device="cuda")
+    bad_inputs = [good.float(), good.transpose(1, 2), good.reshape(-1)[:-1], good.cpu()]
+    for b in bad_inputs:
+        with pytest.raises(ValueError):
+            lb.nusselt_fields_noalloc(p, b, good, good, out)
+        with pytest.raises(ValueError):
+            lb.nusselt_fields_noalloc(p, good, good, b, out)
+    with pytest.raises(ValueError):
+        lb.nusselt_fields_noalloc(p, good, good, good, out[:-1])
+    vdw = lb.Params(**{**p.__dict__, "psi_kind": lb.LB_PSI_VDW})
+    with pytest.raises(ValueError):
+        lb.nusselt_fields_noalloc(vdw, good, good, good, out)
+    torch.cuda.synchronize()
