@@ -156,6 +156,17 @@ int lb_adjoint_step(lb_ctx* ctx, long long nsteps, int checkpoint_every, double*
  * may be NULL. Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
 int lb_populations(lb_ctx* ctx, double* f, double* g, int on_device);
 
+/* lb_set_populations -- replace the current state by a given pre-collision state (f_l, g_l), float64
+ * [19][nx*ny*nz] each in the layout of lb_populations (Eqs. (6)-(7): populations after streaming,
+ * before the collision of the next step); host memory if on_device == 0 (the call synchronises),
+ * device memory otherwise. The values are stored in the context's precision as given (no
+ * validation: the health check of lb_step reports a non-physical state). The step count and the
+ * accumulated Nu samples are kept; a sample due for the replaced state is dropped. Afterwards
+ * lb_adjoint_step gives no dJ/dT0 (the state is no longer lb_init's equilibrium). The paper has no
+ * counterpart (it restarts from stored populations, e.g. for comparisons at an evolved state).
+ * Errors: LB_EINVAL (null argument), LB_ENOMEM, LB_ECUDA. */
+int lb_set_populations(lb_ctx* ctx, const double* f, const double* g, int on_device);
+
 /* lb_diagnostics -- health and conservation of the current state, on the host:
  * out[0] = min rho, out[1] = min T, out[2] = count of non-finite rho/T/u, out[3] = total mass
  * sum rho, out[4] = total sum rho T. FP64 reductions. Errors: LB_EINVAL, LB_ECUDA. */
@@ -196,8 +207,12 @@ int lb_heat_flux_pdf(lb_ctx* ctx, int z_lo, int z_hi, int nbins, double q_lo, do
 
 /* lb_save / lb_load -- checkpoint of (parameters, step count, populations in their storage
  * precision) to a raw binary file with a header and a 64-bit FNV-1a checksum of the payload.
- * lb_load requires a context created with the same grid and precision and replaces its state.
- * Errors: LB_EINVAL, LB_EIO (open/write/read failure, bad magic, mismatch, checksum), LB_ECUDA. */
+ * lb_load requires a context created with the same grid, precision and physics parameters
+ * (tau_nu, tau_kappa, G, kappa, c_v, g_z, T_d, T_u, forcing, psi_kind and, for the van der Waals
+ * psi, its a, b, T_v; the launch shape and sampling periods may differ) and replaces its state,
+ * step count, Nu time average and deviation reference rho0, T0.
+ * Errors: LB_EINVAL, LB_EIO (open/write/read failure, bad magic, grid/precision/parameter
+ * mismatch, checksum), LB_ECUDA. */
 int lb_save(lb_ctx* ctx, const char* path);
 int lb_load(lb_ctx* ctx, const char* path);
 
@@ -229,12 +244,18 @@ const char* lb_last_error(const lb_ctx* ctx);
  * library keeps until the process exits.
  * Inputs (device, float64, node-index order, nx*ny*nz each): rho, uz (physical velocity, z),
  * T, e.g. written by lb_moments with on_device = 1. Output (device, float64): nu_out[0..nz-1] =
- * Nu(z), nu_out[nz] = mean over z. Parameters as in lb_params. Enqueued on cuda_stream
- * (NULL = legacy default stream) of the current device; nothing is synchronised.
+ * Nu(z), nu_out[nz] = mean over z. Parameters as in lb_params. The internal energy is that of
+ * the paper's pseudopotential only, U = c_v T + (G/4) e^{-2/rho}: for fields of a context with
+ * psi_kind = LB_PSI_VDW this call does not give lb_nusselt's Nu (use lb_nusselt there).
+ * Enqueued on cuda_stream (NULL = legacy default stream) of the current device; nothing is
+ * synchronised. Launch failures are read from the launch calls themselves; an error left pending
+ * in the CUDA runtime by the caller's earlier work is neither cleared nor reported.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
- * keeps it; make that first call before any stream capture. Every call shares the array:
- * calls that overlap on the GPU (other streams, other threads) race and must be ordered by the
- * caller. Each call writes every partial it reads, so no state carries over between calls.
+ * keeps it; make that first call before any stream capture. The kept address does not survive
+ * cudaDeviceReset of that device: do not call this entry point after such a reset. Every call
+ * shares the array: calls that overlap on the GPU (other streams, other threads) race and must be
+ * ordered by the caller. Each call writes every partial it reads, so no state carries over between
+ * calls.
  * Errors: LB_EINVAL (null pointer, nx/ny/nz < 1, nz > LB_NOALLOC_MAX_NZ, kappa <= 0, c_v <= 0,
  * T_d == T_u), LB_ECUDA (symbol lookup or launch failed). */
 #define LB_NOALLOC_MAX_NZ 8192

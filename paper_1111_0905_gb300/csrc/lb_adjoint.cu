@@ -352,7 +352,8 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
   using namespace tlbm::adj;
   if (!c) return LB_EINVAL;
   if (nsteps < 1 || checkpoint_every < 1) return lb_fail(c, LB_EINVAL, "nsteps and checkpoint_every must be >= 1");
-  if (dJ_dT0 && c->step != 0) return lb_fail(c, LB_EINVAL, "dJ_dT0 needs the state of lb_init (step 0)");
+  if (dJ_dT0 && (c->step != 0 || !c->from_init))
+    return lb_fail(c, LB_EINVAL, "dJ_dT0 needs the state of lb_init (step 0)");
   if (!(c->p.T_d != c->p.T_u)) return lb_fail(c, LB_EINVAL, "T_d == T_u: Nu is undefined");
   if (c->p.forcing != FORCE_SHIFT || c->p.psi_kind != PSI_EXP)
     return lb_fail(c, LB_EUNSUP, "the adjoint transposes the paper's scheme (velocity shift, psi = exp(-1/rho)) only");

@@ -490,6 +490,30 @@ int lb_populations(lb_ctx* c, double* f, double* g, int on_device) {
   return LB_OK;
 }
 
+int lb_set_populations(lb_ctx* c, const double* f, const double* g, int on_device) {
+  if (!c) return LB_EINVAL;
+  if (!f || !g) return lb_fail(c, LB_EINVAL, "f and g are both required");
+  const size_t n = (size_t)Q * c->N;
+  const double* df = f;
+  const double* dg = g;
+  if (!on_device) {
+    if (!c->pops && cudaMalloc(&c->pops, 2 * n * sizeof(double)) != cudaSuccess)
+      return lb_fail(c, LB_ENOMEM, "population staging");
+    LB_CU(c, cudaMemcpyAsync(c->pops, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LB_CU(c, cudaMemcpyAsync(c->pops + n, g, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    df = c->pops;
+    dg = c->pops + n;
+  }
+  // a Nu sample due for the replaced state is dropped; the buffer written is the current one
+  c->sample_pending = false;
+  KArgs a = make_args(c);
+  a.fout = c->f[c->cur]; a.gout = c->g[c->cur];
+  LB_CU(c, c->ops->setpops(a, df, dg, c->stream));
+  if (!on_device) LB_CU(c, cudaStreamSynchronize(c->stream));
+  c->from_init = false;
+  return LB_OK;
+}
+
 int lb_save(lb_ctx* c, const char* path) {
   if (!c || !path) return c ? lb_fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
   const int frc = flush_sample(c);    // the saved time average includes every due sample
@@ -527,6 +551,19 @@ int lb_load(lb_ctx* c, const char* path) {
   if (std::memcmp(h.magic, "TLBMCKP2", 8) != 0 || h.version != 2) return lb_fail(c, LB_EIO, "bad magic/version");
   if (h.nx != c->p.nx || h.ny != c->p.ny || h.nz != c->p.nz || h.precision != c->p.precision)
     return lb_fail(c, LB_EIO, "grid or precision mismatch");
+  // the physics parameters must be the context's: a state saved under other relaxation times,
+  // coupling, conductivity, gravity, wall temperatures or scheme variant is refused (the
+  // reference state rho0, T0 of the deviation storage is restored from the file)
+  {
+    const lb_params& q = h.params;
+    const lb_params& p = c->p;
+    const bool same = q.tau_nu == p.tau_nu && q.tau_kappa == p.tau_kappa && q.G == p.G &&
+                      q.kappa == p.kappa && q.c_v == p.c_v && q.g_z == p.g_z && q.T_d == p.T_d &&
+                      q.T_u == p.T_u && q.forcing == p.forcing && q.psi_kind == p.psi_kind &&
+                      (p.psi_kind != PSI_VDW ||
+                       (q.vdw_a == p.vdw_a && q.vdw_b == p.vdw_b && q.vdw_T == p.vdw_T));
+    if (!same) return lb_fail(c, LB_EIO, "checkpoint parameters differ from the context's");
+  }
   if (fnv1a(1469598103934665603ull, buf.data(), buf.size()) != h.checksum)
     return lb_fail(c, LB_EIO, "checksum mismatch");
   LB_CU(c, cudaMemcpyAsync(c->f[c->cur], buf.data(), pbytes, cudaMemcpyHostToDevice, c->stream));

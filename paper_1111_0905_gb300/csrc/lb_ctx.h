@@ -28,6 +28,9 @@ struct lb_ctx {
   // passing (fused step + diagnostics); lb_nusselt, lb_diagnostics, lb_save and
   // lb_adjoint_step take it first with a separate moments pass
   bool sample_pending = false;
+  // the state is lb_init's equilibrium of its fields (or its successors by lb_step); false once
+  // lb_set_populations replaced it (dJ/dT0 of lb_adjoint_step needs the former)
+  bool from_init = true;
   std::string err;
 };
 

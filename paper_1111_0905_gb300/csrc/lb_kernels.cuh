@@ -824,6 +824,52 @@ __global__ void lb_init_kernel(const KArgs a, const double* __restrict__ rho_in,
   }
 }
 
+// Given pre-collision state (float64 [19][N] each, the layout of lb_pops_kernel's output) stored
+// as the post-collision buffer B whose pull with the wall rules returns it: B_l(y) = f_l(y + c_l)
+// where y + c_l is inside; otherwise B_l(y) is the bounce-back source of f_{opp(l)} at y, so
+// B_l(y) = f_{opp(l)}(y), and for g the thermal wall rule is inverted:
+// B^g_l(y) = 2 (even part of g^eq_{opp(l)} at T_w, rho_p) - g_{opp(l)}(y) with rho_p the sum of the
+// stored f-slots of y (the density the step forms at the wall node). Stored as deviations.
+template <class S>
+__global__ void lb_setpops_kernel(const KArgs a, const double* __restrict__ f_in,
+                                  const double* __restrict__ g_in) {
+  using R = typename Store<S>::R;
+  S* __restrict__ fo = static_cast<S*>(a.fout);
+  S* __restrict__ go = static_cast<S*>(a.gout);
+  const int nx = a.nx, ny = a.ny, nz = a.nz, plane = a.plane, N = a.N;
+  const R rho0 = R(a.rho0), T0 = R(a.T0), lam = R(a.lam);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+    const int x = idx % nx, y = (idx / nx) % ny, z = idx / plane;
+    R fb[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const int zn = z + CZ(l);
+      const bool wall = (zn < 0 || zn >= nz);
+      const int src = wall ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
+      const int le = wall ? OPP(l) : l;   // population of the given state this slot returns
+      const R df = R(f_in[(size_t)le * N + src] - a.fbase[CSQ(le)]);
+      Store<S>::st(fo + (size_t)l * N + idx, df);
+      fb[l] = Store<S>::rt(df);
+    }
+    R dp = fb[0];
+#pragma unroll
+    for (int m = 1; m < Q; ++m) dp = dp + fb[m];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const int zn = z + CZ(l);
+      const bool wall = (zn < 0 || zn >= nz);
+      const int src = wall ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
+      const int le = wall ? OPP(l) : l;
+      R dg = R(g_in[(size_t)le * N + src] - a.gbase[CSQ(le)]);
+      if (wall) {
+        const R Tw = (CZ(le) > 0) ? R(a.T_d) : R(a.T_u);
+        dg = R(2) * wall_even_dev<R>(le, dp, rho0, T0, Tw, lam) - dg;
+      }
+      Store<S>::st(go + (size_t)l * N + idx, dg);
+    }
+  }
+}
+
 // Pre-collision state (pull + wall rules) exported as float64 [19][N].
 template <class S>
 __global__ void lb_pops_kernel(const KArgs a, double* __restrict__ fo, double* __restrict__ go) {

@@ -16,6 +16,8 @@ struct PrecOps {
   // launch description of the step kernel for a tile height and variant: out = {threads per
   // CTA, dynamic shared memory bytes, resident CTAs per SM, registers per thread}
   cudaError_t (*info)(int by, int var, int out[4]);
+  // store a given pre-collision state (float64 [19][N] f and g on the device) as the buffer
+  cudaError_t (*setpops)(const KArgs&, const double*, const double*, cudaStream_t);
 };
 
 extern const PrecOps kOpsF64, kOpsF32, kOpsBF16, kOpsF16;
@@ -120,6 +122,10 @@ template <class S> struct OpsImpl {
   }
   static cudaError_t init(const KArgs& a, const double* rho, const double* T, cudaStream_t st) {
     lb_init_kernel<S><<<blocks_for(a.N), 256, 0, st>>>(a, rho, T);
+    return cudaGetLastError();
+  }
+  static cudaError_t setpops(const KArgs& a, const double* f, const double* g, cudaStream_t st) {
+    lb_setpops_kernel<S><<<blocks_for(a.N), 256, 0, st>>>(a, f, g);
     return cudaGetLastError();
   }
   static cudaError_t pops(const KArgs& a, double* f, double* g, cudaStream_t st) {

@@ -27,7 +27,7 @@ _lib = None
 EXPORTS = ("lb_init", "lb_step", "lb_adjoint_step", "lb_profiles", "lb_histogram_T_rho",
            "lb_structure_functions", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
            "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error",
-           "lb_nusselt_fields_noalloc", "lb_launch_info", "lb_heat_flux_pdf")
+           "lb_nusselt_fields_noalloc", "lb_launch_info", "lb_heat_flux_pdf", "lb_set_populations")
 NOALLOC_MAX_NZ = 8192
 
 
@@ -110,6 +110,8 @@ def load_library():
     lib.lb_nusselt.restype = I
     lib.lb_populations.argtypes = [P, P, P, I]
     lib.lb_populations.restype = I
+    lib.lb_set_populations.argtypes = [P, P, P, I]
+    lib.lb_set_populations.restype = I
     lib.lb_diagnostics.argtypes = [P, P]
     lib.lb_diagnostics.restype = I
     lib.lb_save.argtypes = [P, ctypes.c_char_p]
@@ -168,10 +170,33 @@ def _current_stream():
     return None
 
 
+def _check_device_f64(name: str, t, min_numel: int, exact: bool) -> None:
+    """A CUDA float64 contiguous tensor of (at least, unless exact) min_numel elements."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a CUDA float64 tensor, got {type(t).__name__}")
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA float64 tensor "
+                         f"(dtype {t.dtype}, device {t.device}, contiguous {t.is_contiguous()})")
+    if (t.numel() != min_numel) if exact else (t.numel() < min_numel):
+        raise ValueError(f"{name} has {t.numel()} elements, needs {'' if exact else 'at least '}{min_numel}")
+
+
 def nusselt_fields_noalloc(params: Params, rho, uz, T, nu_out, stream=None) -> None:
     """lb_nusselt_fields_noalloc on CUDA tensors (inputs [nz, ny, nx] float64; nu_out nz + 1
-    float64); enqueued on the current stream, allocates no device memory."""
+    float64); enqueued on the current stream, allocates no device memory. The tensors are checked
+    here (dtype, device, contiguity, sizes) before any pointer reaches the device; the call
+    supports the paper's pseudopotential only (params.psi_kind = LB_PSI_EXP)."""
+    if params.psi_kind != LB_PSI_EXP:
+        raise ValueError("lb_nusselt_fields_noalloc uses the internal energy of psi = exp(-1/rho) only")
     lib = load_library()
+    if params.nx >= 1 and params.ny >= 1 and 1 <= params.nz <= NOALLOC_MAX_NZ:
+        n = params.nx * params.ny * params.nz
+        for name, t in (("rho", rho), ("uz", uz), ("T", T)):
+            _check_device_f64(name, t, n, exact=True)
+        _check_device_f64("nu_out", nu_out, params.nz + 1, exact=False)
+    # sizes outside the entry point's limits go through unchecked: it rejects them (LB_EINVAL)
+    # before touching any pointer
     st = _current_stream() if stream is None else stream
     rc = lib.lb_nusselt_fields_noalloc(_ptr(rho), _ptr(uz), _ptr(T), params.nx, params.ny, params.nz,
                                        params.kappa, params.G, params.c_v, params.T_d, params.T_u,
@@ -310,6 +335,24 @@ class Lattice:
             g = np.empty(shape, dtype=np.float64)
         self._check(self.lib.lb_populations(self.ctx, _ptr(f), _ptr(g), int(device)), "lb_populations")
         return f, g
+
+    def set_populations(self, f, g) -> None:
+        """lb_set_populations: replace the state by pre-collision (f, g), each [19, nz, ny, nx]
+        float64 (numpy / host tensors, or CUDA tensors)."""
+        n = Q * self.params.N
+        if isinstance(f, np.ndarray) or isinstance(g, np.ndarray):
+            f, g = _host_f64(f, n), _host_f64(g, n)
+            on_device = False
+        else:
+            import torch
+            if f.dtype != torch.float64 or g.dtype != torch.float64:
+                raise ValueError("populations must be float64")
+            if f.numel() != n or g.numel() != n or bool(f.is_cuda) != bool(g.is_cuda):
+                raise ValueError("population size or placement does not match")
+            f, g = f.contiguous(), g.contiguous()
+            on_device = bool(f.is_cuda)
+        self._check(self.lib.lb_set_populations(self.ctx, _ptr(f), _ptr(g), int(on_device)),
+                    "lb_set_populations")
 
     def diagnostics(self) -> dict:
         out = np.empty(5, dtype=np.float64)

@@ -147,3 +147,30 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_noalloc_binding_refuses_host_tensors_and_the_vdw_psi_without_a_gpu(lblib):
+    """The binding of lb_nusselt_fields_noalloc refuses, before any call into the library,
+    numpy arrays, CPU tensors, float32 tensors and a context of the van der Waals psi (whose
+    internal energy the entry point does not implement)."""
+    import torch
+    p = config.boiling_cell(4).params
+    n = p.nx * p.ny * p.nz
+    host = torch.zeros(n, dtype=torch.float64)
+    out = torch.zeros(p.nz + 1, dtype=torch.float64)
+    for bad in (np.zeros(n), host, host.float()):
+        with pytest.raises(ValueError):
+            lb.nusselt_fields_noalloc(p, bad, host, host, out)
+    vdw = lb.Params(**{**p.__dict__, "psi_kind": lb.LB_PSI_VDW})
+    with pytest.raises(ValueError, match="exp"):
+        lb.nusselt_fields_noalloc(vdw, host, host, host, out)
+
+
+def test_boiling_block_equals_the_same_block_of_the_full_cell():
+    """The block generator (used for the oracle's samples of the 512^3 cell) draws the same values
+    as the full-cell recipe at those nodes, including blocks that touch the grid's far corner."""
+    r, T = synthetic.boiling_fields(20, 12, 9, 1.5, 0.35, 0.31)
+    for (x0, y0, z0, sx, sy, sz) in ((3, 2, 4, 7, 5, 3), (0, 0, 0, 20, 12, 9), (13, 7, 6, 7, 5, 3)):
+        b, Tb = synthetic.boiling_block(20, 12, 9, x0, y0, z0, sx, sy, sz, 1.5, 0.35, 0.31)
+        assert np.array_equal(b, r[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx])
+        assert np.array_equal(Tb, T[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx])
