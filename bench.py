@@ -1,12 +1,13 @@
 #!/usr/bin/env python
 """Benchmark of the fused thermal D3Q19 lattice Boltzmann step on GB300.
 
-Workload: the single-phase thermal convection cell 128^3 (compressed liquid rho = 2.30 between
-a hot bottom and a cold top wall, Pr = 9, seeded 1 % temperature noise), the FP32 form as the
-headline, with the FP64, BF16-deviation and FP16-deviation forms of the same cell reported
-beside it with their error against the FP64 step. One "step" is one full time step of the
-method (pull streaming, moments, psi, force, velocities, divergence, f and g collisions, walls)
-= one fused kernel launch. Value = lattice-node updates per second (GLUPS) of the whole job.
+Headline workload: the paper-geometry boiling cell 512^3 (L = 512 as in the paper's Table 1;
+rho = 1.50 (1 + 0.01 xi) inside coexistence between a hot bottom and a cold top wall, Pr = 9,
+Ra = half the largest value the adiabatic gradient allows at L = 512), FP32 form. The FP16- and
+BF16-deviation and FP64 forms of the same cell are timed beside it and stated with their error
+against the FP64 step. One "step" is one full time step of the method (pull streaming, moments,
+psi, force, velocities, divergence, f and g collisions, walls) = one fused kernel launch.
+Value = lattice-node updates per second (GLUPS) of the whole job.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -35,13 +36,22 @@ UNIT = "GLUPS"
 Q = 19
 FORMS = {"f64": 0, "f32": 1, "bf16dev": 2, "fp16dev": 3}
 STORE_BYTES = {"f64": 8, "f32": 4, "bf16dev": 2, "fp16dev": 2}
-ERR_STEPS = 200
+KERNEL_TYPE = {"f64": "double", "f32": "float", "bf16dev": "__nv_bfloat16", "fp16dev": "__half"}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the fused step
-# kernel from an ncu capture, keyed by the hash of the kernel sources it was taken on; it is
-# reported as null when the sources have changed since.
-TRAFFIC = {"src_hash": "53645933b324c7a2",
-           "bytes_per_launch": {"f32": 337961472 + 276750080, "fp16dev": 167004160 + 117662976}}
+# kernel from an ncu capture of a smaller cell (`nodes` nodes; a capture with more than the
+# launch time is kept to a few GB on the device), keyed by the hash of the kernel sources it
+# was taken on. The headline's traffic is that capture scaled by the node count (the traffic
+# of one launch grows in proportion to the nodes it updates); null once the sources changed.
+TRAFFIC = {"src_hash": "none", "nodes": 192 ** 3, "bytes_per_launch": {},
+           "what": "ncu DRAM bytes of one launch of the 192^3 paper-geometry cell, scaled by the node count"}
+
+# FP64 operations per node of the FP64 step kernel (ncu: 2 x DFMA + DADD + DMUL thread
+# instructions of one launch of the 128^3 single-phase cell, divided by the nodes; this counts
+# the ring recomputation, i.e. the work the kernel issues), and GB300's nominal FP64 rate
+# (152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s; no measured FP64 peak).
+FP64_FLOPS_PER_NODE = None
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 STEP_KERNEL_SOURCES = ("lb_kernels.cuh", "lb_launch.cuh", "lb_prec_f32.cu", "lb_prec_f16.cu")
@@ -138,26 +148,53 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(prec_name: str, n: int = 128):
-    """The headline 128^3 single-phase cell, or (n > 128, profiling with --only) the
-    paper-geometry boiling cell of the size sweep."""
+HEADLINE_N = 512
+# Forms timed at the headline size, the headline form first. FP64 is bound by its FP64
+# instructions (about 134 ms per step at 512^3), so it is timed over fewer steps.
+FORM_ORDER = ("f32", "fp16dev", "bf16dev", "f64")
+F64_MAX_STEPS = 20
+ERR_STEPS_HEADLINE = 100
+C5_STEPS = 1000
+
+
+def workload(prec_name: str, n: int = HEADLINE_N):
+    """The paper-geometry boiling cell (n^3; 512^3 is the headline), or with n = 128 the
+    single-phase convection cell."""
     from paper_1111_0905_gb300 import config
-    if n > 128:
-        return config.paper_scale_cell(n, precision=FORMS[prec_name])
-    return config.single_phase_cell(128, precision=FORMS[prec_name])
+    if n == 128:
+        return config.single_phase_cell(128, precision=FORMS[prec_name])
+    return config.paper_scale_cell(n, precision=FORMS[prec_name])
+
+
+def describe(w) -> str:
+    p = w.params
+    if w.kind == "boiling":
+        return (f"paper-geometry boiling cell {p.nx}x{p.ny}x{p.nz} (rho = 1.50 (1 + 0.01 xi) inside "
+                f"coexistence, T_d/T_u = T_m (1 +- 0.05), tau_nu = {p.tau_nu:g}, tau_kappa = "
+                f"{p.tau_kappa:g}, Pr = 9, Ra = 0.5 Ra_max(L = {p.nz}))")
+    return (f"single-phase thermal convection cell {p.nx}x{p.ny}x{p.nz} (rho = 2.30, Pr = 9, "
+            f"tau_nu = {p.tau_nu:g}, tau_kappa = {p.tau_kappa:g}, Ra = 0.5 Ra_max)")
 
 
 def config_dict(w, form: str) -> dict:
     p = w.params
     N = p.nx * p.ny * p.nz
     in_bytes = 2 * Q * N * STORE_BYTES[form]
-    return {"workload": f"single-phase thermal convection cell {p.nx}x{p.ny}x{p.nz} "
-                        f"(rho=2.30, Pr=9, tau_nu={p.tau_nu:g}, tau_kappa={p.tau_kappa:g}, "
-                        f"Ra=0.5*Ra_max), {form} form",
+    return {"workload": f"{describe(w)}, {form} form",
             "grid": [p.nx, p.ny, p.nz], "nodes": N, "form": form,
-            "l2": f"inputs larger than L2: {in_bytes / 1e6:.0f} MB of populations read per step "
+            "l2": f"inputs larger than L2: {in_bytes / 1e9:.2f} GB of populations read per step "
                   f"> 129 MB L2; no flush",
             "parallelism": "replicas", "lattice": "D3Q19 x2 (f, g)"}
+
+
+def _device_errors(ref, got) -> dict:
+    """max |got - ref| / max |ref| per field on the device (u on the largest |u| component)."""
+    r0, u0, T0 = ref
+    r1, u1, T1 = got
+    us = max(float(u0[a].abs().max()) for a in range(3))
+    return {"rho": float((r1 - r0).abs().max() / r0.abs().max()),
+            "T": float((T1 - T0).abs().max() / T0.abs().max()),
+            "u": max(float((u1[a] - u0[a]).abs().max()) for a in range(3)) / us}
 
 
 def run_ours(args):
@@ -189,93 +226,121 @@ def run_ours(args):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        ctx = clocks if clocks is not None else None
-        if ctx is not None:
-            ctx.__enter__()
+        if clocks is not None:
+            clocks.__enter__()
         e0.record(stream)
         lat.step(K)
         e1.record(stream)
         e1.synchronize()
-        if ctx is not None:
-            ctx.__exit__(None, None, None)
+        if clocks is not None:
+            clocks.__exit__(None, None, None)
         torch.cuda.synchronize()
         barrier()
         return e0.elapsed_time(e1)
 
+    n = args.n
+    main_form = args.only or "f32"
+    w_main = workload(main_form, n)
+    p0 = w_main.params
+    N = p0.nx * p0.ny * p0.nz
+    rho_np, T_np = w_main.fields()
+    rho_d = torch.from_numpy(rho_np).cuda()
+    T_d = torch.from_numpy(T_np).cuda()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+
     results = {}
-    fields = {}
-    main_form = "f32"
     clock_summary = None
-    form_list = [args.only] if args.only else ["f32", "f64", "bf16dev", "fp16dev"]
+    form_list = [args.only] if args.only else list(FORM_ORDER)
     for form in form_list:
-        w = workload(form, args.n if args.only else 128)
-        p = w.params
+        p = workload(form, n).params
         if args.only:
             p.nu_every = args.nu_every
-        N = p.nx * p.ny * p.nz
-        rho, T = w.fields()
-        rho_d = torch.from_numpy(rho).cuda()
-        T_d = torch.from_numpy(T).cuda()
         lat = lb.Lattice(p, rho_d, T_d)
         launch = lat.launch_info()
-        K = args.steps if form == main_form else min(args.steps, 2000)
-        W = args.warmup
-        uuid = None
-        try:
-            uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
-        except Exception:
-            uuid = None
+        K = args.steps if (form == main_form or form != "f64") else min(args.steps, F64_MAX_STEPS)
         sampler = ClockSampler(uuid) if form == main_form else None
-        ms = time_steps(lat, K, W, sampler)
+        ms = time_steps(lat, K, args.warmup, sampler)
         if sampler is not None:
             clock_summary = sampler.summary()
         health = lat.diagnostics()          # outside the timed region: the state stayed physical
+        lat.close()
         ms = max_over_ranks(ms)
         per_step = ms / K
-        lat.close()
-        # error of this form against the FP64 step after ERR_STEPS steps of the same cell
-        lat = lb.Lattice(p, rho_d, T_d)
-        lat.step(ERR_STEPS)
-        r, u, TT = lat.moments()
-        nu = lat.nusselt()[0]
-        lat.close()
-        fields[form] = (r, u, TT, nu)
-        bytes_step = 2 * 2 * Q * N * STORE_BYTES[form]
-        glups_rank = N / (per_step * 1e-3) / 1e9
-        results[form] = {"glups": glups_rank * ws, "ms_per_step": per_step, "steps": K,
+        bytes_step = 4 * Q * N * STORE_BYTES[form]
+        results[form] = {"glups": N / (per_step * 1e-3) / 1e9 * ws, "ms_per_step": per_step,
+                         "steps": K, "warmup": args.warmup,
                          "state_after": {"min_rho": float(health["min_rho"]),
                                          "min_T": float(health["min_T"]),
                                          "nonfinite": int(health["nonfinite"])},
                          "hbm_gbs_algorithmic": bytes_step / (per_step * 1e-3) / 1e9,
                          "hbm_frac": bytes_step / (per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
                          "bytes_per_node": 4 * Q * STORE_BYTES[form], "launch": launch}
-        del rho_d, T_d
         torch.cuda.empty_cache()
 
     if args.only:
         if rank == 0:
-            print(json.dumps({"only": args.only, "form": results[args.only]}))
+            print(json.dumps({"only": args.only, "n": n, "form": results[args.only]}))
         if ws > 1:
             dist.destroy_process_group()
         return None
-    r64, u64, T64, nu64 = fields["f64"]
-    for form, (r, u, TT, nu) in fields.items():
-        results[form]["err_vs_f64"] = None if form == "f64" else {
-            "steps": ERR_STEPS,
-            "rho": float(np.abs(r - r64).max() / np.abs(r64).max()),
-            "T": float(np.abs(TT - T64).max() / np.abs(T64).max()),
-            "u": float(max(np.abs(u[a] - u64[a]).max() for a in range(3)) /
-                       max(np.abs(u64[a]).max() for a in range(3))),
-            "nu_mean": float(abs(nu - nu64) / max(abs(nu64), 1e-300))}
+
+    # error of each form against the FP64 step after ERR_STEPS_HEADLINE steps of the same cell,
+    # compared on the device
+    ref = None
+    shape = (p0.nz, p0.ny, p0.nx)
+    for form in ("f64", "f32", "fp16dev", "bf16dev"):
+        lat = lb.Lattice(workload(form, n).params, rho_d, T_d)
+        lat.step(ERR_STEPS_HEADLINE)
+        outs = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
+        lat.moments_into(*outs, device=True)
+        nu = lat.nusselt()[0]
+        lat.close()
+        fields = (outs[0], outs[1:4], outs[4])
+        if form == "f64":
+            ref, nu64 = fields, nu
+            results["f64"]["err_vs_f64"] = None
+            results["f64"]["nu_mean_after"] = nu
+        else:
+            e = _device_errors(ref, fields)
+            e.update({"steps": ERR_STEPS_HEADLINE, "nu_mean": nu, "nu_mean_f64": nu64,
+                      "nu_rel_err": abs(nu - nu64) / abs(nu64)})
+            results[form]["err_vs_f64"] = e
+            del outs, fields
+        torch.cuda.empty_cache()
+    del ref
+    torch.cuda.empty_cache()
+    for form in ("f32", "fp16dev", "bf16dev"):
+        results[form]["speedup_vs_f64"] = results[form]["glups"] / results["f64"]["glups"]
+    results["f64"]["fp64_alu"] = fp64_alu_roofline(results["f64"]["ms_per_step"], N)
+
+    # C5 itself: 1000 timed steps of the FP32 and FP16-deviation forms at 512^3
+    c5 = {}
+    if not args.no_sizes and n == HEADLINE_N:
+        for form in ("f32", "fp16dev"):
+            if form == main_form and args.steps == C5_STEPS:
+                c5[form] = {"glups": results[form]["glups"], "ms_per_step": results[form]["ms_per_step"],
+                            "hbm_frac": results[form]["hbm_frac"], "steps": C5_STEPS}
+                continue
+            lat = lb.Lattice(workload(form, n).params, rho_d, T_d)
+            ms = max_over_ranks(time_steps(lat, C5_STEPS, args.warmup)) / C5_STEPS
+            lat.close()
+            bytes_step = 4 * Q * N * STORE_BYTES[form]
+            c5[form] = {"glups": N / (ms * 1e-3) / 1e9 * ws, "ms_per_step": ms, "steps": C5_STEPS,
+                        "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+            torch.cuda.empty_cache()
+    del rho_d, T_d
+    torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: H2D of the initial fields from pinned
     # memory, K steps, Nu and the moment fields back to pinned host memory
-    w = workload(main_form)
-    p = w.params
-    N = p.nx * p.ny * p.nz
-    rho, T = w.fields()
-    rho_h = torch.from_numpy(rho).pin_memory()
-    T_h = torch.from_numpy(T).pin_memory()
+    p = w_main.params
+    rho_h = torch.from_numpy(rho_np).pin_memory()
+    T_h = torch.from_numpy(T_np).pin_memory()
+    del rho_np, T_np
     outs = [torch.empty((p.nz, p.ny, p.nx), dtype=torch.float64).pin_memory() for _ in range(5)]
     torch.cuda.synchronize()
     barrier()
@@ -290,13 +355,14 @@ def run_ours(args):
     e2e = {"value": N * args.steps * ws / t_e2e / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 2 * N * 8 / args.steps,
            "d2h_bytes_per_step": (5 * N * 8 + (p.nz + 1) * 8 + 16) / args.steps,
+           "seconds": t_e2e, "nu_mean": nu_mean,
            "what": "lb_init from pinned host rho,T + lb_step(K) + lb_nusselt + lb_moments to "
-                   "pinned host, wall clock"}
+                   "pinned host, wall clock, headline cell and form"}
+    del outs, rho_h, T_h
 
-    # the sizes the HBM target is stated at (256^3, 512^3), same kernel, paper-geometry boiling cell
     sizes = {} if args.no_sizes else size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws)
     variants = {} if args.no_sizes else variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws)
-    diagnostics = diagnostics_cost(lb, torch, max_over_ranks, barrier, results[main_form]["ms_per_step"])
+    diagnostics = {} if args.no_sizes else diagnostics_cost(lb, torch, max_over_ranks, barrier, sizes)
     adjoint = {} if args.no_sizes else adjoint_cost(lb, torch)
     horizons = {} if args.no_sizes else horizon_errors(lb, torch, np)
 
@@ -304,13 +370,17 @@ def run_ours(args):
     src_hash = kernel_src_hash()
     traffic = None
     if TRAFFIC["src_hash"] == src_hash:
-        traffic = TRAFFIC["bytes_per_launch"].get(main_form)
+        t = TRAFFIC["bytes_per_launch"].get(main_form)
+        traffic = None if t is None else t * N / TRAFFIC["nodes"]
     bytes_launch = 4 * Q * STORE_BYTES[main_form] * N
     roofline = {"bound": "hbm", "achieved": bytes_launch / (main["ms_per_step"] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": bytes_launch / (main["ms_per_step"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                "traffic": traffic, "peak_src": peaks["src"] + " (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": "tlbm::lb_fused_kernel<float,8,0>", "algorithmic_bytes_per_launch": bytes_launch}
+                "traffic": traffic, "peak_src": peaks["src"] + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "traffic_src": TRAFFIC["what"] if traffic is not None else "kernel sources changed since the capture",
+                "kernel": f"tlbm::lb_fused_kernel<{KERNEL_TYPE[main_form]},8,0,0>",
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "algorithmic": f"76 values x {STORE_BYTES[main_form]} B x {N} nodes (19 f + 19 g read and written)"}
 
     out = None
     if rank == 0:
@@ -319,10 +389,10 @@ def run_ours(args):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded SplitMix64 fields; no dataset)",
-               "config": config_dict(w, main_form), "roofline": roofline, "cpu_baseline": cpu,
+               "config": config_dict(w_main, main_form), "roofline": roofline, "cpu_baseline": cpu,
                "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_summary,
-               "forms": results, "sizes": sizes, "variants": variants, "diagnostics": diagnostics,
-               "adjoint": adjoint, "horizon_errors": horizons,
+               "forms": results, "c5_1000_steps": c5, "sizes": sizes, "variants": variants,
+               "diagnostics": diagnostics, "adjoint": adjoint, "horizon_errors": horizons,
                "kernel_src_hash": src_hash}
         print(json.dumps(out))
     if ws > 1:
@@ -330,91 +400,107 @@ def run_ours(args):
     return out
 
 
-def size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
-    """GLUPS and HBM fraction of the FP32 and FP16-deviation forms on the boiling cell at 256^3
-    and 512^3 (50 timed steps after 10 warm-up steps each)."""
-    from paper_1111_0905_gb300 import config
-    out = {}
-    for n in (256, 512):
-        for form in ("f32", "fp16dev"):
-            w = config.paper_scale_cell(n, precision=FORMS[form])
-            p = w.params
-            N = p.nx * p.ny * p.nz
-            rho, T = w.fields()
-            lat = lb.Lattice(p, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
-            launch = lat.launch_info()
-            del rho, T
-            lat.step(10)
-            torch.cuda.synchronize()
-            barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            K = 50
-            e0.record()
-            lat.step(K)
-            e1.record()
-            e1.synchronize()
-            ms = max_over_ranks(e0.elapsed_time(e1)) / K
-            lat.close()
-            torch.cuda.empty_cache()
-            bytes_step = 4 * Q * STORE_BYTES[form] * N
-            out[f"{n}^3_{form}"] = {"glups": N / (ms * 1e-3) / 1e9 * ws, "ms_per_step": ms,
-                                    "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                                    "workload": w.name, "launch": launch}
-    return out
+def fp64_alu_roofline(ms_per_step: float, N: int) -> dict:
+    """FP64 form against GB300's FP64 pipe: FP64 operations per node (counted by ncu) x nodes per
+    step / step time, against the nominal FP64 rate."""
+    if FP64_FLOPS_PER_NODE is None:
+        return {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "what": "FP64 operation count not captured for these sources"}
+    achieved = FP64_FLOPS_PER_NODE * N / (ms_per_step * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_node": FP64_FLOPS_PER_NODE,
+            "peak_src": "nominal: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
 
 
-def diagnostics_cost(lb, torch, max_over_ranks, barrier, ms_step: float) -> dict:
-    """Cost of sampling Nu(z) and the health values every step (nu_every = 1: one moments pass
-    and one finalisation per step) on the FP32 128^3 cell, 200 timed steps after 10 warm-up."""
-    w = workload("f32")
-    p = w.params
-    p.nu_every = 1
-    rho, T = w.fields()
+def _timed(lb, torch, max_over_ranks, barrier, p, rho, T, K, W=10):
     lat = lb.Lattice(p, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
-    lat.step(10)
+    launch = lat.launch_info()
+    lat.step(W)
     torch.cuda.synchronize()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    K = 200
-    e0.record()
+    st = torch.cuda.current_stream()
+    e0.record(st)
     lat.step(K)
-    e1.record()
+    e1.record(st)
     e1.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1)) / K
+    health = lat.diagnostics()
     lat.close()
-    return {"nu_every": 1, "ms_per_step": ms, "ms_per_sample": ms - ms_step,
-            "step_only_ms": ms_step}
+    torch.cuda.empty_cache()
+    return ms, launch, health
+
+
+def size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
+    """GLUPS and HBM fraction of every form on the 128^3 single-phase convection cell and of the
+    FP32 and FP16-deviation forms on the 256^3 paper-geometry boiling cell (200 timed steps
+    after 10 warm-up steps; FP64 50 steps)."""
+    out = {}
+    for n, forms in ((128, ("f32", "fp16dev", "bf16dev", "f64")), (256, ("f32", "fp16dev"))):
+        for form in forms:
+            w = workload(form, n)
+            p = w.params
+            N = p.nx * p.ny * p.nz
+            rho, T = w.fields()
+            K = 50 if form == "f64" else 200
+            ms, launch, health = _timed(lb, torch, max_over_ranks, barrier, p, rho, T, K)
+            bytes_step = 4 * Q * STORE_BYTES[form] * N
+            out[f"{n}^3_{form}"] = {"glups": N / (ms * 1e-3) / 1e9 * ws, "ms_per_step": ms, "steps": K,
+                                    "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                    "workload": describe(w), "launch": launch,
+                                    "nonfinite": int(health["nonfinite"])}
+    return out
+
+
+def diagnostics_cost(lb, torch, max_over_ranks, barrier, sizes) -> dict:
+    """Cost of sampling Nu(z) and the health values every step (nu_every = 1: the step launch
+    takes the sample in passing, plus the finalisation) on the FP32 128^3 cell, 200 timed steps
+    after 10 warm-up, against the same cell without samples."""
+    w = workload("f32", 128)
+    p = w.params
+    p.nu_every = 1
+    rho, T = w.fields()
+    ms, _, _ = _timed(lb, torch, max_over_ranks, barrier, p, rho, T, 200)
+    ms_step = sizes.get("128^3_f32", {}).get("ms_per_step")
+    return {"workload": describe(w) + ", f32 form", "nu_every": 1, "ms_per_step": ms,
+            "ms_per_sample": None if ms_step is None else ms - ms_step, "step_only_ms": ms_step}
 
 
 def adjoint_cost(lb, torch) -> dict:
     """The discrete adjoint on the 64^3 boiling cell (FP64, 1000 steps, checkpoints every 50):
-    wall time of lb_adjoint_step (J and dJ/d(T_d, T_u, G)) against the forward run that computes
-    J (1000 steps with a Nu sample each, then lb_nusselt), both from lb_init's state."""
+    wall time of lb_adjoint_step (J and dJ/d(T_d, T_u, G)) against (a) the plain forward run,
+    lb_step(1000) with no Nu sampling, and (b) the forward run that computes J (1000 steps with
+    a Nu sample each, then lb_nusselt), all from lb_init's state."""
     from paper_1111_0905_gb300 import config
     w = config.boiling_cell(64, kappa=0.15, tau_nu=1.25)
     p = w.params
     rho, T = w.fields()
     N, K = 1000, 50
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, r
+
     lat = lb.Lattice(p, rho, T)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    got = lat.adjoint(N, K)
-    torch.cuda.synchronize()
-    t_adj = time.perf_counter() - t0
+    lat.step(5)                    # warm-up of the kernels, then a fresh context for each run
+    lat.close()
+    lat = lb.Lattice(p, rho, T)
+    t_adj, got = wall(lambda: lat.adjoint(N, K))
+    lat.close()
+    lat = lb.Lattice(p, rho, T)
+    t_plain, _ = wall(lambda: lat.step(N))
     lat.close()
     q = lb.Params(**{**p.__dict__, "nu_every": 1})
     lat = lb.Lattice(q, rho, T)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lat.step(N)
-    J = lat.nusselt()[2]
-    torch.cuda.synchronize()
-    t_fwd = time.perf_counter() - t0
+    t_fwd, J = wall(lambda: (lat.step(N), lat.nusselt()[2])[1])
     lat.close()
     return {"workload": "boiling cell 64^3 FP64, 1000 steps, checkpoints every 50",
-            "adjoint_s": t_adj, "forward_s": t_fwd, "ratio": t_adj / t_fwd,
+            "adjoint_s": t_adj, "forward_plain_s": t_plain, "forward_with_J_s": t_fwd,
+            "ratio_vs_plain_step": t_adj / t_plain, "ratio_vs_forward_with_J": t_adj / t_fwd,
             "J": got["J"], "J_rel_diff_vs_forward": abs(got["J"] - J) / abs(J),
             "dJ_dTd": got["T_d"], "dJ_dTu": got["T_u"], "dJ_dG": got["G"]}
 
@@ -495,27 +581,31 @@ def variant_sweep(lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
     return out
 
 
-def _oracle_sample(side: int):
-    """Oracle state and params of a side^3 sample of the benchmark cell."""
+def _oracle_block(side: int):
+    """Oracle state and params of a side^3 block of the headline cell: the corner block on the
+    bottom wall of the 512^3 paper-geometry boiling cell, with that cell's parameters (its
+    gravity, conductivity, relaxation times and wall temperatures) and its own initial values at
+    those nodes (drawn from the same generator counters)."""
     import torch
     from oracle import lbm
-    from paper_1111_0905_gb300 import config
-    w = config.single_phase_cell(128)
+    from paper_1111_0905_gb300 import synthetic
+    w = workload("f64", HEADLINE_N)
     p = w.params
     op = lbm.Params(side, side, side, p.tau_nu, p.tau_kappa, p.G, p.kappa, p.c_v, p.g_z, p.T_d, p.T_u)
-    from paper_1111_0905_gb300 import synthetic
-    rho, T = synthetic.single_phase_fields(side, side, side, 2.30, p.T_d, p.T_u)
+    rho, T = synthetic.boiling_block(p.nx, p.ny, p.nz, 0, 0, 0, side, side, side, w.rho_mean,
+                                     p.T_d, p.T_u)
     f, g = lbm.init_state(torch.from_numpy(rho), torch.from_numpy(T), op)
     return f, g, op
 
 
 def cpu_baseline(args) -> dict:
-    """FP64 oracle timed on the host cores on a bounded sample of the full 128^3 cell: as many
-    steps as take about 15 s (6 to 100), after one warm-up step; then on one host thread, as many
-    steps as take about 8 s (1 to 20)."""
+    """FP64 oracle timed on the host cores on a bounded sample of the headline cell: a 128^3
+    block of the 512^3 cell, as many steps as take about 15 s (6 to 100) after one warm-up step;
+    then on one host thread, as many steps as take about 8 s (1 to 20)."""
     import torch
     from oracle import lbm
-    f, g, op = _oracle_sample(128)
+    side = 128
+    f, g, op = _oracle_block(side)
     t0 = time.perf_counter()
     f, g = lbm.step(f, g, op)  # warm-up, also sizes the sample
     n = max(6, min(100, int(15.0 / max(time.perf_counter() - t0, 1e-3))))
@@ -523,7 +613,6 @@ def cpu_baseline(args) -> dict:
     for _ in range(n):
         f, g = lbm.step(f, g, op)
     dt = time.perf_counter() - t0
-    # the same oracle on one host thread (a few steps of the same cell)
     threads = torch.get_num_threads()
     torch.set_num_threads(1)
     try:
@@ -536,16 +625,16 @@ def cpu_baseline(args) -> dict:
         dt1 = time.perf_counter() - t1
     finally:
         torch.set_num_threads(threads)
-    return {"value": 128 ** 3 * n / dt / 1e9, "unit": UNIT, "cores": threads,
-            "kind": "oracle", "sample": f"{n} steps of the 128^3 cell (FP64 oracle, PyTorch CPU)",
-            "seconds": dt,
-            "single_thread": {"value": 128 ** 3 * n1 / dt1 / 1e9, "unit": UNIT, "cores": 1,
-                              "sample": f"{n1} steps of the 128^3 cell", "seconds": dt1}}
+    what = f"{side}^3 block of the {HEADLINE_N}^3 paper-geometry boiling cell (FP64 oracle, PyTorch CPU)"
+    return {"value": side ** 3 * n / dt / 1e9, "unit": UNIT, "cores": threads,
+            "kind": "oracle", "sample": f"{n} steps of a {what}", "seconds": dt,
+            "single_thread": {"value": side ** 3 * n1 / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} steps of the same block", "seconds": dt1}}
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step is one oracle step of a cube sample of the
-    benchmark cell, the cube sized so that warm-up + timed steps stay within about two minutes."""
+    """The oracle as the reference arm: each step is one FP64 oracle step of a cube block of the
+    headline cell, the cube sized so that warm-up + timed steps stay within about two minutes."""
     import torch
     from oracle import lbm
     ws, rank, local = dist_env()
@@ -553,13 +642,13 @@ def run_reference(args):
         return None
     side = 8
     for s in (32, 16, 8):
-        f, g, op = _oracle_sample(s)
+        f, g, op = _oracle_block(s)
         t0 = time.perf_counter()
         lbm.step(f, g, op)
         if (time.perf_counter() - t0) * (args.steps + args.warmup) < 120.0:
             side = s
             break
-    f, g, op = _oracle_sample(side)
+    f, g, op = _oracle_block(side)
     for _ in range(args.warmup):
         f, g = lbm.step(f, g, op)
     t0 = time.perf_counter()
@@ -568,14 +657,17 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     nodes = side ** 3
     value = nodes * args.steps / dt / 1e9
-    from paper_1111_0905_gb300 import config
-    w = config.single_phase_cell(128, precision=1)
-    sample = f"each step = one FP64 oracle step of a {side}^3 sample of the 128^3 cell"
+    w = workload("f64", HEADLINE_N)
+    sample = (f"each step = one FP64 oracle step of a {side}^3 block (corner on the bottom wall) of "
+              f"the {HEADLINE_N}^3 cell")
+    cfg = config_dict(w, "f64")
+    cfg.update({"workload": f"{side}^3 block of the {describe(w)}, FP64 oracle on the host cores",
+                "grid": [side, side, side], "nodes": nodes, "sample_of": [w.params.nx] * 3})
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded SplitMix64 fields; no dataset)",
-           "config": config_dict(w, "f32"),
+           "config": cfg,
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(),
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -586,17 +678,20 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
-    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=C5_STEPS)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-sizes", action="store_true", help="skip the 256^3/512^3 measurements")
-    ap.add_argument("--only", choices=list(FORMS), help="time one form of the 128^3 cell only "
-                    "(no errors, e2e or baselines; for profiling)")
+    ap.add_argument("--no-sizes", action="store_true",
+                    help="skip the extra entries (1000-step C5 timings, 128^3/256^3, variants, "
+                         "diagnostics, adjoint, horizon errors)")
+    ap.add_argument("--only", choices=list(FORMS), help="time one form only (no errors, e2e or "
+                    "baselines; for profiling)")
     ap.add_argument("--nu-every", type=int, default=0, help="with --only: sample Nu every n steps "
                     "inside the timed steps (the diagnostics path)")
-    ap.add_argument("--n", type=int, default=128, choices=[128, 256, 512],
-                    help="with --only: cube size (256/512: the boiling cell of the size sweep)")
+    ap.add_argument("--n", type=int, default=HEADLINE_N, choices=[128, 192, 256, 512],
+                    help="cube size (default 512, the headline; 128: the single-phase convection "
+                         "cell; 192/256: the boiling cell; smaller sizes for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

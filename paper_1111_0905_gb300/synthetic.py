@@ -57,3 +57,21 @@ def single_phase_fields(nx, ny, nz, rho_mean, T_d, T_u, amp=0.01, seed=SEED):
     rho = np.full((nz, ny, nx), rho_mean, dtype=np.float64)
     T = linear_T(nx, ny, nz, T_d, T_u) * (1.0 + amp * noise_field(nx, ny, nz, seed))
     return rho, T
+
+
+def noise_block(nx, ny, nz, x0, y0, z0, sx, sy, sz, seed=SEED) -> np.ndarray:
+    """The [z0, z0+sz) x [y0, y0+sy) x [x0, x0+sx) block of noise_field(nx, ny, nz, seed), drawn
+    row by row from the generator's counter (no full field is formed), shaped [sz, sy, sx]."""
+    out = np.empty((sz, sy, sx), dtype=np.float64)
+    for k in range(sz):
+        for j in range(sy):
+            out[k, j] = uniform_pm1(sx, seed, offset=x0 + nx * ((y0 + j) + ny * (z0 + k)))
+    return out
+
+
+def boiling_block(nx, ny, nz, x0, y0, z0, sx, sy, sz, rho_mean, T_d, T_u, amp=0.01, seed=SEED):
+    """The same block of boiling_fields(nx, ny, nz, ...): density and temperature values equal to
+    those of the full cell at the block's nodes."""
+    rho = rho_mean * (1.0 + amp * noise_block(nx, ny, nz, x0, y0, z0, sx, sy, sz, seed))
+    T = linear_T(1, 1, nz, T_d, T_u)[z0:z0 + sz, 0, 0]
+    return rho, np.broadcast_to(T[:, None, None], (sz, sy, sx)).copy()
