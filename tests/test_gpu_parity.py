@@ -102,7 +102,7 @@ def test_fp64_single_phase_full_size_128(lblib, cuda):
 def test_fp32_parity(lblib, cuda):
     w = config.single_phase_cell(32, precision=lb.LB_FP32)
     rho, T = w.fields()
-    errs = _compare(w.params, rho, T, 50, 1e-5, nu_tol=1e-3, pops=True)
+    errs = _compare(w.params, rho, T, 50, 1e-5, nu_tol=1e-5, pops=True)
     print("FP32 errors:", errs)
 
 
@@ -113,7 +113,7 @@ def test_fp32_ragged_tiles(lblib, cuda, by, zc):
     p = w.params
     p.tile_y, p.z_chunk = by, zc
     rho, T = w.fields()
-    _compare(p, rho, T, 20, 1e-5, nu_tol=1e-3, pops=True)
+    _compare(p, rho, T, 20, 1e-5, nu_tol=1e-5, pops=True)
 
 
 def test_fp64_rejects_the_16_row_tile(lblib, cuda):
@@ -130,7 +130,7 @@ def test_fp64_rejects_the_16_row_tile(lblib, cuda):
 def test_fp32_boiling_parity(lblib, cuda):
     w = config.boiling_cell(24, precision=lb.LB_FP32)
     rho, T = w.fields()
-    errs = _compare(w.params, rho, T, 30, 1e-5, nu_tol=1e-2, pops=True)
+    errs = _compare(w.params, rho, T, 30, 1e-5, nu_tol=1e-5, pops=True)
     print("FP32 boiling errors:", errs)
 
 
@@ -338,7 +338,7 @@ def test_variant_parity_fp64(lblib, cuda, forcing, psi):
 @pytest.mark.parametrize("forcing,psi", VARIANTS)
 def test_variant_parity_fp32(lblib, cuda, forcing, psi):
     p, rho, T = _variant_cell(forcing, psi, lb.LB_FP32)
-    _compare(p, rho, T, 15, 1e-5, nu_tol=1e-3)
+    _compare(p, rho, T, 15, 1e-5, nu_tol=1e-5)
 
 
 def test_variant_parity_16bit(lblib, cuda):
@@ -435,3 +435,164 @@ def test_nu_sampling_with_health_checks_and_checkpoints(lblib, cuda, tmp_path):
     d.step(5)
     assert d.nusselt()[2] == full
     d.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(lb.LB_FP64, 1e-12), (lb.LB_FP32, 1e-5)])
+def test_wall_force_of_a_z_profile_on_the_gpu(lblib, cuda, prec, tol):
+    """The neutral-wetting wall ghosts on the GPU against the closed form (not the oracle): for a
+    density that varies in z only, at the initial state (j = 0, no gravity) the exported physical
+    velocity is u = F/(2 rho) with F_x = F_y = 0 and F_z(z) = -(G/2) psi(z) [psi(z+1) - psi(z-1)],
+    the plane beyond each halfway wall carrying the density of its mirror image (psi(-1) = psi(0),
+    psi(nz) = psi(nz-1)). Ragged tiles (40 x 9) and several z chunks."""
+    nx, ny, nz = 40, 9, 7
+    z = np.arange(nz, dtype=np.float64)
+    prof = 1.3 + 0.4 * np.tanh(z - 1.0) - 0.3 * np.exp(-(nz - 1 - z))
+    rho = np.broadcast_to(prof[:, None, None], (nz, ny, nx)).copy()
+    T = np.full((nz, ny, nx), config.T_M)
+    p = lb.Params(nx=nx, ny=ny, nz=nz, tau_nu=1.0, tau_kappa=1.0, G=config.G_DEFAULT, kappa=0.05,
+                  g_z=0.0, T_d=config.T_M, T_u=config.T_M, precision=prec, tile_y=4, z_chunk=3)
+    lat = lb.Lattice(p, rho, T)
+    r, u, TT = lat.moments()
+    lat.close()
+    ps = np.exp(-1.0 / prof)
+    ext = np.concatenate([[ps[0]], ps, [ps[-1]]])          # planes -1 .. nz
+    Fz = -(p.G / 2.0) * ps * (ext[2:] - ext[:-2])
+    want = Fz / (2.0 * prof)
+    scale = np.abs(want).max()
+    assert scale > 1e-3
+    got = u[2][:, 0, 0]
+    assert np.abs(u[2] - want[:, None, None]).max() <= tol * scale, (got, want)
+    assert np.abs(u[0]).max() <= tol * scale and np.abs(u[1]).max() <= tol * scale
+
+
+def _evolved_state(steps: int = 300):
+    """Pre-collision populations of the 32 x 24 x 20 boiling cell (tau_nu = 1.25, kappa = 0.15)
+    after `steps` FP64 GPU steps: phase separation under way, with flow at the interfaces."""
+    w = config.boiling_cell(32, nz=20, ny=24, kappa=0.15, tau_nu=1.25)
+    p = w.params
+    rho, T = w.fields()
+    lat = lb.Lattice(p, rho, T)
+    lat.step(steps)
+    f, g = lat.populations()
+    lat.close()
+    return p, rho, T, f, g
+
+
+def _oracle_from(p, f, g, steps):
+    op = oracle_params(p)
+    ft, gt = torch.from_numpy(f), torch.from_numpy(g)
+    for _ in range(steps):
+        ft, gt = lbm.step(ft, gt, op)
+    return ft, gt, op
+
+
+def _conv_scale(f, g, op):
+    """Scale of the convective term of Nu(z): max over z of <|rho U u_z|>_{x,y} / (kappa dT/nz)."""
+    r, j, T, F, v, u = lbm.macroscopic(f, g, op)
+    U = lbm.internal_energy(r, T, op)
+    q = (r * U * u[2]).abs().mean(dim=(1, 2)) / (op.kappa * (op.T_d - op.T_u) / op.nz)
+    return float(q.max())
+
+
+def test_set_populations_continues_the_run_exactly(lblib, cuda):
+    """lb_set_populations stores a given pre-collision state so that the next steps continue it:
+    an FP64 context seeded with the state after 300 steps equals the oracle started from it
+    (1e-12), and its populations read back unchanged."""
+    p, rho, T, f, g = _evolved_state()
+    lat = lb.Lattice(p, rho, T)
+    lat.set_populations(f, g)
+    assert lat.step_count == 0
+    with pytest.raises(lb.LBError) as e:
+        lat.adjoint(2, 1, grad_T0=True)      # no longer lb_init's equilibrium
+    assert e.value.code == -1
+    f1, g1 = lat.populations()
+    assert rel_err(f1, f) < 1e-15 and rel_err(g1, g) < 1e-15
+    lat.step(10)
+    r, u, TT = lat.moments()
+    ft, gt, op = _oracle_from(p, f, g, 10)
+    r_o, u_o, T_o = lbm.moments_out(ft, gt, op)
+    assert rel_err(r, r_o) < 1e-12 and rel_err(TT, T_o) < 1e-12
+    us = max(float(np.abs(u_o[a].numpy()).max()) for a in range(3))
+    assert max(float(np.abs(u[a] - u_o[a].numpy()).max()) for a in range(3)) < 1e-12 * us
+    lat.close()
+
+
+def _fp32_from(p, rho, T, f, g, steps):
+    """FP32 form and oracle from the same FP64 pre-collision state (the FP32 context created from
+    the run's initial fields, so that its deviation reference is the run's); errors as in the
+    parity tests, u on the largest |u| of the oracle (no floor), Nu(z) on its convective scale."""
+    q = lb.Params(**{**p.__dict__, "precision": lb.LB_FP32})
+    lat = lb.Lattice(q, rho, T)
+    lat.set_populations(f, g)
+    lat.step(steps)
+    r, u, TT = lat.moments()
+    nu = lat.nusselt()[1]
+    lat.close()
+    ft, gt, op = _oracle_from(p, f, g, steps)
+    r_o, u_o, T_o = lbm.moments_out(ft, gt, op)
+    us = max(float(np.abs(u_o[a].numpy()).max()) for a in range(3))
+    errs = {"rho": rel_err(r, r_o), "T": rel_err(TT, T_o), "u_max": us}
+    errs["u"] = max(float(np.abs(u[a] - u_o[a].numpy()).max()) for a in range(3)) / us
+    nu_o = lbm.nusselt(ft, gt, op)[1].numpy()
+    cs = _conv_scale(ft, gt, op)
+    errs["nu_z_on_conv"] = float(np.abs(nu - nu_o).max()) / cs
+    errs["conv_scale"] = cs
+    return errs
+
+
+def test_fp32_parity_on_a_convecting_state(lblib, cuda):
+    """FP32 form against the oracle from developed convection, element by element at the FP32
+    tolerance of 1e-5 relative with no velocity floor: the 128^3 single-phase cell after 2000 FP64
+    GPU steps (Nu about 1.67), then 10 steps of each. rho, T, every velocity component on the
+    largest |u|, and Nu(z) on the scale of its convective term <|rho U u_z|>/(kappa dT/nz)."""
+    w = config.single_phase_cell(128)
+    p = w.params
+    rho, T = w.fields()
+    lat = lb.Lattice(p, rho, T)
+    lat.step(2000)
+    f, g = lat.populations()
+    lat.close()
+    errs = _fp32_from(p, rho, T, f, g, 10)
+    print("FP32 convecting-state errors:", errs)
+    assert errs["u_max"] > 3e-3, errs
+    assert max(errs["rho"], errs["T"], errs["u"]) < 1e-5, errs
+    assert errs["nu_z_on_conv"] < 1e-5, errs
+
+
+def test_fp32_parity_on_a_phase_separating_state(lblib, cuda):
+    """FP32 form against the oracle from a phase-separating state (the 32 x 24 x 20 boiling cell
+    after 300 FP64 GPU steps, interface flow |u| ~ 3e-3), 20 steps: rho and T within 1e-5. The
+    velocity and the convective Nu term are compared relative (no floor) with the bound the
+    arithmetic gives here: the spinodal dynamics amplify the FP32 rounding of the O(0.1) force
+    sum of Eq. (9) over the 20 steps to an absolute velocity error ~1e-7 (measured 4.1e-5 of the
+    largest |u|, 1.4e-5 of the convective Nu scale), so 1e-4 and 5e-5."""
+    p, rho, T, f, g = _evolved_state()
+    errs = _fp32_from(p, rho, T, f, g, 20)
+    print("FP32 phase-separating-state errors:", errs)
+    assert errs["u_max"] > 3e-3, errs
+    assert max(errs["rho"], errs["T"]) < 1e-5, errs
+    assert errs["u"] < 1e-4, errs
+    assert errs["nu_z_on_conv"] < 5e-5, errs
+
+
+def test_checkpoint_of_other_physics_parameters_is_refused(lblib, cuda, tmp_path):
+    """lb_load refuses a checkpoint saved under other physics parameters (here tau_nu, then the
+    wall temperature); other launch shapes and sampling periods load."""
+    w = config.boiling_cell(12, nz=8, ny=8)
+    rho, T = w.fields()
+    a = lb.Lattice(w.params, rho, T)
+    a.step(3)
+    a.save(tmp_path / "a.bin")
+    a.close()
+    for field, value in (("tau_nu", 1.1), ("T_d", w.params.T_d * 1.01), ("forcing", lb.LB_FORCE_GUO)):
+        q = lb.Params(**{**w.params.__dict__, field: value})
+        b = lb.Lattice(q, rho, T)
+        with pytest.raises(lb.LBError) as e:
+            b.load(tmp_path / "a.bin")
+        assert e.value.code == -5 and b.step_count == 0
+        b.close()
+    q = lb.Params(**{**w.params.__dict__, "tile_y": 4, "z_chunk": 3, "nu_every": 2})
+    b = lb.Lattice(q, rho, T)
+    b.load(tmp_path / "a.bin")
+    assert b.step_count == 3
+    b.close()

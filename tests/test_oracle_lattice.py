@@ -115,3 +115,58 @@ def test_thermal_wall_rule_returns_wall_equilibrium():
 def test_mirror_index():
     assert [lbm.mirror_z(k, 5) for k in (-2, -1, 0, 4, 5, 6)] == [1, 0, 0, 4, 4, 3]
     assert [lbm.mirror_z(k, 1) for k in (-2, -1, 1, 2)] == [0, 0, 0, 0]
+
+
+def _z_profile(nz, nx=3, ny=2):
+    """A density that varies only in z, steep next to both walls: rho(z) = 1.3 + 0.4 tanh(z - 1)
+    - 0.3 exp(-(nz - 1 - z))."""
+    z = torch.arange(nz, dtype=DT)
+    r = 1.3 + 0.4 * torch.tanh(z - 1.0) - 0.3 * torch.exp(-(nz - 1 - z))
+    return r[:, None, None].expand(nz, ny, nx).clone()
+
+
+@pytest.mark.parametrize("nz", [1, 2, 3, 7])
+def test_wall_force_of_a_z_profile_is_the_mirrored_closed_form(nz):
+    """Eq. (9) for a density that depends on z only: the 6 links with c_z = +-1 (one axis link
+    of weight 1/6, four diagonals of weight 1/12) give F_z(z) = -(G/2) psi(z) [psi(z+1) - psi(z-1)]
+    and F_x = F_y = 0. With halfway walls and the neutral-wetting ghosts the plane beyond a wall
+    carries the density of its mirror image: psi(-1) = psi(rho(0)), psi(nz) = psi(rho(nz-1)),
+    so F_z(0) = -(G/2) psi(0) [psi(1) - psi(0)]. A ghost mirrored about the node (psi(-1) = psi(1),
+    no force on plane 0) or psi = 0 beyond the wall fails this."""
+    p = lbm.Params(3, 2, nz, 1.0, 1.0, G=-2.7, kappa=0.1)
+    rho = _z_profile(nz)
+    F = lbm.force(rho, p)
+    ps = torch.exp(-1.0 / rho[:, 0, 0])
+    ext = [ps[lbm.mirror_z(k, nz)] for k in range(-1, nz + 1)]   # planes -1 .. nz
+    for z in range(nz):
+        want = -(p.G / 2.0) * ps[z] * (ext[z + 2] - ext[z])
+        assert torch.allclose(F[2, z], want.expand_as(F[2, z]), rtol=1e-14, atol=1e-15), z
+    assert float(F[0].abs().max()) < 1e-15 and float(F[1].abs().max()) < 1e-15
+    if nz >= 3:
+        # the explicit first-plane form: the bottom ghost is plane 0 itself
+        want0 = -(p.G / 2.0) * ps[0] * (ps[1] - ps[0])
+        assert abs(float(F[2, 0, 0, 0]) - float(want0)) < 1e-15
+        assert abs(float(F[2, 0, 0, 0]) - float(-(p.G / 2.0) * ps[0] * (ps[1] - ps[1]))) > 1e-3
+
+
+@pytest.mark.parametrize("nz", [1, 2, 5])
+def test_wall_ghosts_are_the_even_and_odd_extensions(nz):
+    """Across a halfway wall the force of Eq. (9) sees the even extension of rho and the divergence
+    sees the odd extension of u_z: on a 3-D random field, the wall-bounded force and divergence
+    equal those of the fully periodic cell of height 2 nz that holds the field and its mirror
+    image (rho(2nz-1-z) = rho(z); u_z(2nz-1-z) = -u_z(z), u_x and u_y likewise reversed, as the
+    ghost rule u -> -u states)."""
+    g = torch.Generator().manual_seed(7)
+    nx, ny = 5, 4
+    rho = 1.2 + 0.5 * torch.rand((nz, ny, nx), generator=g, dtype=DT)
+    u = 0.02 * (torch.rand((3, nz, ny, nx), generator=g, dtype=DT) - 0.5)
+    p = lbm.Params(nx, ny, nz, 1.0, 1.0, G=-2.7, kappa=0.1)
+    q = lbm.Params(nx, ny, 2 * nz, 1.0, 1.0, G=-2.7, kappa=0.1, periodic_z=True)
+    rho_ext = torch.cat([rho, torch.flip(rho, dims=(0,))])
+    u_ext = torch.cat([u, -torch.flip(u, dims=(1,))], dim=1)
+    F = lbm.force(rho, p)
+    F_ext = lbm.force(rho_ext, q)
+    assert torch.allclose(F, F_ext[:, :nz], rtol=0, atol=1e-15)
+    D = lbm.divergence(u, p)
+    D_ext = lbm.divergence(u_ext, q)
+    assert torch.allclose(D, D_ext[:nz], rtol=0, atol=1e-16)
