@@ -34,9 +34,13 @@ sys.path.insert(0, str(ROOT))
 METRIC = "GLUPS and % HBM roofline per full step; mixed vs FP64 at stated error"
 UNIT = "GLUPS"
 Q = 19
-FORMS = {"f64": 0, "f32": 1, "bf16dev": 2, "fp16dev": 3}
-STORE_BYTES = {"f64": 8, "f32": 4, "bf16dev": 2, "fp16dev": 2}
-KERNEL_TYPE = {"f64": "double", "f32": "float", "bf16dev": "__nv_bfloat16", "fp16dev": "__half"}
+FORMS = {"f64": 0, "f32": 1, "bf16dev": 2, "fp16dev": 3, "fp16loc": 4}
+STORE_BYTES = {"f64": 8, "f32": 4, "bf16dev": 2, "fp16dev": 2, "fp16loc": 2}
+# values stored per lattice and node: the 19 populations, plus two reference slots for the FP16
+# storage against local references (its extra traffic counts against its roofline fraction)
+STORED_SLOTS = {"f64": 19, "f32": 19, "bf16dev": 19, "fp16dev": 19, "fp16loc": 21}
+KERNEL_TYPE = {"f64": "double", "f32": "float", "bf16dev": "__nv_bfloat16", "fp16dev": "__half",
+               "fp16loc": "tlbm::half_loc"}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the fused step
 # kernel from an ncu capture of a smaller cell (`nodes` nodes; a capture with more than the
@@ -151,7 +155,7 @@ def dist_env():
 HEADLINE_N = 512
 # Forms timed at the headline size, the headline form first. FP64 is bound by its FP64
 # instructions (about 134 ms per step at 512^3), so it is timed over fewer steps.
-FORM_ORDER = ("f32", "fp16dev", "bf16dev", "f64")
+FORM_ORDER = ("f32", "fp16loc", "fp16dev", "bf16dev", "f64")
 F64_MAX_STEPS = 20
 ERR_STEPS_HEADLINE = 100
 C5_STEPS = 1000
@@ -278,7 +282,9 @@ def run_ours(args):
                                          "nonfinite": int(health["nonfinite"])},
                          "hbm_gbs_algorithmic": bytes_step / (per_step * 1e-3) / 1e9,
                          "hbm_frac": bytes_step / (per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                         "bytes_per_node": 4 * Q * STORE_BYTES[form], "launch": launch}
+                         "bytes_per_node": 4 * Q * STORE_BYTES[form],
+                         "stored_bytes_per_node": 4 * STORED_SLOTS[form] * STORE_BYTES[form],
+                         "launch": launch}
         torch.cuda.empty_cache()
 
     if args.only:
@@ -292,7 +298,7 @@ def run_ours(args):
     # compared on the device
     ref = None
     shape = (p0.nz, p0.ny, p0.nx)
-    for form in ("f64", "f32", "fp16dev", "bf16dev"):
+    for form in ("f64", "f32", "fp16loc", "fp16dev", "bf16dev"):
         lat = lb.Lattice(workload(form, n).params, rho_d, T_d)
         lat.step(ERR_STEPS_HEADLINE)
         outs = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
@@ -313,14 +319,14 @@ def run_ours(args):
         torch.cuda.empty_cache()
     del ref
     torch.cuda.empty_cache()
-    for form in ("f32", "fp16dev", "bf16dev"):
+    for form in ("f32", "fp16loc", "fp16dev", "bf16dev"):
         results[form]["speedup_vs_f64"] = results[form]["glups"] / results["f64"]["glups"]
     results["f64"]["fp64_alu"] = fp64_alu_roofline(results["f64"]["ms_per_step"], N)
 
     # C5 itself: 1000 timed steps of the FP32 and FP16-deviation forms at 512^3
     c5 = {}
     if not args.no_sizes and n == HEADLINE_N:
-        for form in ("f32", "fp16dev"):
+        for form in ("f32", "fp16loc", "fp16dev"):
             if form == main_form and args.steps == C5_STEPS:
                 c5[form] = {"glups": results[form]["glups"], "ms_per_step": results[form]["ms_per_step"],
                             "hbm_frac": results[form]["hbm_frac"], "steps": C5_STEPS}
@@ -437,7 +443,7 @@ def size_sweep(args, lb, torch, peaks, max_over_ranks, barrier, ws) -> dict:
     FP32 and FP16-deviation forms on the 256^3 paper-geometry boiling cell (200 timed steps
     after 10 warm-up steps; FP64 50 steps)."""
     out = {}
-    for n, forms in ((128, ("f32", "fp16dev", "bf16dev", "f64")), (256, ("f32", "fp16dev"))):
+    for n, forms in ((128, ("f32", "fp16loc", "fp16dev", "bf16dev", "f64")), (256, ("f32", "fp16loc", "fp16dev"))):
         for form in forms:
             w = workload(form, n)
             p = w.params
@@ -507,8 +513,8 @@ def adjoint_cost(lb, torch) -> dict:
 
 def horizon_errors(lb, torch, np) -> dict:
     """Errors of the mixed forms against the FP64 step at the stated horizons of the two
-    configurations they are quoted on: the 128^3 single-phase cell after 2000 steps (FP32, BF16,
-    FP16 deviations) and the 256^3 boiling cell after 5000 steps (FP32, BF16, FP16 deviations).
+    configurations they are quoted on: the 128^3 single-phase cell after 2000 steps and the 256^3
+    boiling cell after 5000 steps (FP32, FP16 against local references, BF16 and FP16 deviations).
     Field errors are max |form - FP64| / max |FP64| (u on the largest |u|), with the root mean
     square of the rho error beside it; Nu_mean of each run and the relative mass change."""
     from paper_1111_0905_gb300 import config
@@ -516,7 +522,7 @@ def horizon_errors(lb, torch, np) -> dict:
     for name, make, n, steps in (("single_phase_128^3", config.single_phase_cell, 128, 2000),
                                  ("boiling_256^3", config.paper_scale_cell, 256, 5000)):
         runs = {}
-        for form in ("f64", "f32", "bf16dev", "fp16dev"):
+        for form in ("f64", "f32", "fp16loc", "bf16dev", "fp16dev"):
             w = make(n, precision=FORMS[form])
             rho, T = w.fields()
             lat = lb.Lattice(w.params, torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
@@ -530,7 +536,7 @@ def horizon_errors(lb, torch, np) -> dict:
             torch.cuda.empty_cache()
         r64, u64, T64, nu64, dm64, _ = runs["f64"]
         entry = {"steps": steps, "f64": {"nu_mean": nu64, "mass_change": dm64}}
-        for form in ("f32", "bf16dev", "fp16dev"):
+        for form in ("f32", "fp16loc", "bf16dev", "fp16dev"):
             r, u, TT, nu, dm, bad = runs[form]
             entry[form] = {
                 "rho": float(np.abs(r - r64).max() / np.abs(r64).max()),

@@ -47,14 +47,20 @@ typedef enum {
   LB_FP64 = 0,     /* float64 storage and compute */
   LB_FP32 = 1,     /* float32 storage and compute */
   LB_BF16_DEV = 2, /* bfloat16 storage of the deviations below, float32 compute */
-  LB_FP16_DEV = 3  /* float16 storage of the deviations below, float32 compute */
+  LB_FP16_DEV = 3, /* float16 storage of the deviations below, float32 compute */
+  LB_FP16_LOC = 4  /* float16 storage against local references (below), float32 compute */
 } lb_precision;
-/* Every precision stores deviations from the reference equilibria, f_l - f^eq_l(rho0, 0, T0) and
- * g_l - g^eq_l(rho0, T0, 0), and forms moments and equilibria from them. The rounding of the
- * stored deviations is not mass-conserving: measured against the float64 step, float32 stays
- * within 1e-5 on rho and T over 2000 steps (5e-5 over 5000 boiling steps); float16 within 2e-3
- * over 2000 single-phase steps but not over long boiling runs; bfloat16 only over short runs
- * (a few hundred steps). */
+/* LB_FP64 .. LB_FP16_DEV store deviations from the reference equilibria, f_l - f^eq_l(rho0, 0, T0)
+ * and g_l - g^eq_l(rho0, T0, 0), and form moments and equilibria from them. LB_FP16_LOC stores,
+ * per population, its deviation minus the rest equilibrium of the node that wrote it (its density
+ * and temperature at that step, per lattice direction class, kept in FP16 in two extra slots per
+ * lattice and node: 21 instead of 19 stored values), so that FP16 rounds the non-equilibrium and
+ * velocity parts only. Measured against the float64 step (max over the field relative to its
+ * scale): float32 stays within 1e-6 on rho and T over 2000 single-phase steps and 5e-5 over 5000
+ * boiling steps of the 256^3 cell; float16 deviations within 2e-3 over 2000 single-phase steps but
+ * not over long boiling runs (4e-2 after 5000 steps: the phase pattern drifts); bfloat16 deviations
+ * only over short runs (a few hundred steps); float16 against local references within 2e-3 over
+ * both horizons. */
 
 /* Scheme variants for comparison with the paper's scheme (variant 0 of each; the paper defines
  * neither alternative). Forcing: LB_FORCE_SHIFT, the paper's equilibrium velocity

@@ -360,7 +360,7 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
   const long long K = checkpoint_every < nsteps ? checkpoint_every : nsteps;
   const long long nck = (nsteps + K - 1) / K;
   const size_t N = (size_t)c->N;
-  const size_t pbytes = (size_t)Q * N * c->ops->esize;
+  const size_t pbytes = (size_t)c->ops->slots * N * c->ops->esize;
   const size_t sbytes = 2 * (size_t)Q * N * sizeof(double);
   cudaStream_t st = c->stream;
   Geom g{c->p.nx, c->p.ny, c->p.nz, c->plane, c->N};

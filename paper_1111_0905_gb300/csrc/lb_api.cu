@@ -128,6 +128,7 @@ const PrecOps* ops_for(int prec) {
     case LB_FP32: return &kOpsF32;
     case LB_BF16_DEV: return &kOpsBF16;
     case LB_FP16_DEV: return &kOpsF16;
+    case LB_FP16_LOC: return &kOpsF16Loc;
     default: return nullptr;
   }
 }
@@ -152,6 +153,10 @@ KArgs make_args(const lb_ctx* c) {
   a.pf = {(float)a.tau_nu, (float)a.omega_nu, (float)a.omega_kappa, (float)a.G, (float)a.g_z,
           (float)a.lam, (float)a.inv_cv, (float)a.T_d, (float)a.T_u, (float)a.rho0, (float)a.T0,
           (float)a.E0, (float)c->p.vdw_a, (float)c->p.vdw_b, (float)c->p.vdw_T, (float)vk};
+  a.pd.psi0 = std::exp(-1.0 / c->rho0);
+  a.pd.irho0 = 1.0 / c->rho0;
+  a.pf.psi0 = (float)a.pd.psi0;
+  a.pf.irho0 = (float)a.pd.irho0;
   // reference equilibria per class (rest, axis, diagonal): f^eq(rho0, 0, T0), g^eq(rho0, T0, 0)
   const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
   for (int k = 0; k < 3; ++k) {
@@ -267,7 +272,7 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
   int by = p.tile_y != 0 ? p.tile_y : 8;
   if (by != 4 && by != 8 && by != 16) return LB_EINVAL;
   if (!ops->tile_ok(by)) return LB_EINVAL;
-  if ((long long)Q * N >= (1ll << 32)) return LB_EINVAL;   // 32-bit population offsets
+  if ((long long)ops->slots * N >= (1ll << 32)) return LB_EINVAL;   // 32-bit population offsets
   if (p.z_chunk < 0 || p.nu_every < 0 || p.check_every < 0) return LB_EINVAL;
   if (p.forcing != FORCE_SHIFT && p.forcing != FORCE_GUO) return LB_EINVAL;
   if (p.psi_kind != PSI_EXP && p.psi_kind != PSI_VDW) return LB_EINVAL;
@@ -356,7 +361,7 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
 
   // 64 bytes of padding: a word-wide copy of a 16-bit element (stage_word) reads the 4-byte word
   // that contains it
-  const size_t pbytes = (size_t)Q * N * ops->esize + 64;
+  const size_t pbytes = (size_t)ops->slots * N * ops->esize + 64;
   for (int k = 0; k < 2; ++k) {
     if (cudaMalloc(&c->f[k], pbytes) != cudaSuccess || cudaMalloc(&c->g[k], pbytes) != cudaSuccess) {
       cudaFree(staging);
@@ -518,7 +523,7 @@ int lb_save(lb_ctx* c, const char* path) {
   if (!c || !path) return c ? lb_fail(c, LB_EINVAL, "path is null") : LB_EINVAL;
   const int frc = flush_sample(c);    // the saved time average includes every due sample
   if (frc) return frc;
-  const size_t pbytes = (size_t)Q * c->N * c->ops->esize;
+  const size_t pbytes = (size_t)c->ops->slots * c->N * c->ops->esize;
   std::vector<unsigned char> buf(2 * pbytes);
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
@@ -543,7 +548,7 @@ int lb_load(lb_ctx* c, const char* path) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return lb_fail(c, LB_EIO, std::string("cannot open ") + path);
   CkptHeader h;
-  const size_t pbytes = (size_t)Q * c->N * c->ops->esize;
+  const size_t pbytes = (size_t)c->ops->slots * c->N * c->ops->esize;
   std::vector<unsigned char> buf(2 * pbytes);
   bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
   std::fclose(fp);

@@ -60,6 +60,24 @@ template <class R> __host__ __device__ constexpr R FW(int l) {
 // df_l = f_l - f^eq_l(rho0, 0, T0) and dg_l = g_l - g^eq_l(rho0, T0, 0), so that the moments
 // and the collision work on small numbers (the 16-bit forms need it; FP32 gains accuracy).
 // ---------------------------------------------------------------------------------------
+// FP16 storage against local references. Each lattice holds, after its 19 population slots, two
+// reference slots per node: for the node y that wrote them, the deviations of the rest
+// equilibria f^eq(rho_y, 0, T_y) and g^eq(rho_y, T_y, 0) (of the colliding step) per class,
+//   f: a1 = w1 drho, a2 = w2 (4.5 dE - 0.5 drho)  (axis, diagonal), a0 = 12 (a1 - a2) (rest),
+//   g: b1 = w1 dE,   b2 = w2 (4.5 lam dT - 0.5 dE), b0 = 12 (b1 - b2),
+// drho = rho - rho0, dE = rho T - rho0 T0, dT = T - T0, themselves rounded to FP16 (so that the
+// writer and every reader use the same values). A population slot holds its deviation minus the
+// reference of its class at the node that wrote it, rounded to FP16: a pull of population l from
+// node y adds y's reference back. The stored numbers are then the non-equilibrium and velocity
+// parts of the populations (|u| ~ 1e-2) instead of the density and temperature contrast between
+// the node and the global reference state (O(1) across a liquid-vapour interface), which is
+// what FP16's 11-bit significand rounds.
+struct __align__(2) half_loc { __half h; };
+template <class S> struct IsLoc { static constexpr bool v = false; };
+template <> struct IsLoc<half_loc> { static constexpr bool v = true; };
+// population slots per lattice: 19, plus the two reference slots of the local-reference storage
+template <class S> __host__ __device__ constexpr int slots() { return IsLoc<S>::v ? Q + 2 : Q; }
+
 template <class S> struct Store;
 template <> struct Store<double> {
   using R = double;
@@ -85,6 +103,15 @@ template <> struct Store<__half> {
   static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
   static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
 };
+template <> struct Store<half_loc> {
+  using R = float;
+  static __device__ __forceinline__ float ld(const half_loc* p) {
+    return __half2float(__ldg(reinterpret_cast<const __half*>(p)));
+  }
+  static __device__ __forceinline__ void st(half_loc* p, float v) { p->h = __float2half_rn(v); }
+  static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
+};
+
 
 
 // Parameters of the hot path in the compute precision R, precomputed on the host so that the
@@ -92,6 +119,7 @@ template <> struct Store<__half> {
 template <class R> struct KPar {
   R tau_nu, omega_nu, omega_kappa, G, g_z, lam, inv_cv, T_d, T_u, rho0, T0, E0;
   R va, vb, vT, vk;   // van der Waals-type psi: a, b, T_v, 2/(-G)
+  R psi0, irho0;      // psi(rho0) = exp(-1/rho0) and 1/rho0 (deviation form of psi)
 };
 
 // Scheme variants (comparisons with the paper's scheme, which is variant 0 of each).
@@ -141,6 +169,9 @@ __host__ __device__ __forceinline__ int mirror_z(int k, int nz) {
   return m < nz ? m : 2 * nz - 1 - m;
 }
 
+template <class S>
+__device__ __forceinline__ float loc_ref(const S* __restrict__ buf, unsigned e, int ls, unsigned N);
+
 // Pull the 19 populations of node (col[1], row[1], pz): v_l = buf_l(x - c_l). Across a wall the
 // bounce-back source buf_{opp(l)}(x) is returned (the g wall rule is applied by the caller).
 template <class S, class R>
@@ -152,8 +183,12 @@ __device__ __forceinline__ void pull(R (&v)[Q], const S* __restrict__ buf, int N
     const int zs = pz - CZ(l);
     if (zs < 0 || zs >= nz) {
       v[l] = Store<S>::ld(buf + (size_t)OPP(l) * N + own);
+      if constexpr (IsLoc<S>::v)
+        v[l] = v[l] + loc_ref<S>(buf, (unsigned)OPP(l) * (unsigned)N + (unsigned)own, OPP(l), (unsigned)N);
     } else {
-      v[l] = Store<S>::ld(buf + (size_t)l * N + (zs * plane + row[1 - CY(l)] + col[1 - CX(l)]));
+      const size_t e = (size_t)l * N + (size_t)(zs * plane + row[1 - CY(l)] + col[1 - CX(l)]);
+      v[l] = Store<S>::ld(buf + e);
+      if constexpr (IsLoc<S>::v) v[l] = v[l] + loc_ref<S>(buf, (unsigned)e, l, (unsigned)N);
     }
   }
 }
@@ -187,13 +222,26 @@ __device__ __forceinline__ R wall_even_dev(int l, R drho_p, R rho0, R T0, R Tw, 
   return WT<R>(l) * (dP + R(4.5) * (lam * (Tw - T0) - dP / R(3)) * R(CSQ(l) - 1));
 }
 
+template <class S>
+__device__ __forceinline__ float loc_ref(const S* __restrict__ buf, unsigned e, int ls, unsigned N);
+
 template <class S, class R>
 __device__ __forceinline__ void g_wall_fix(R (&g)[Q], const S* __restrict__ fin, int N, int own,
                                            int z, int nz, R rho0, R T0, R Td, R Tu, R lam) {
   if (z != 0 && z != nz - 1) return;
-  R dp = Store<S>::ld(fin + own);
+  R dp;
+  if constexpr (IsLoc<S>::v) {
+    // the stored post-collision f of the wall node, each with its node's reference added back
+    dp = Store<S>::ld(fin + own) + loc_ref<S>(fin, (unsigned)own, 0, (unsigned)N);
 #pragma unroll
-  for (int m = 1; m < Q; ++m) dp = dp + Store<S>::ld(fin + (size_t)m * N + own);
+    for (int m = 1; m < Q; ++m)
+      dp = dp + (Store<S>::ld(fin + (size_t)m * N + own) +
+                 loc_ref<S>(fin, (unsigned)m * (unsigned)N + (unsigned)own, m, (unsigned)N));
+  } else {
+    dp = Store<S>::ld(fin + own);
+#pragma unroll
+    for (int m = 1; m < Q; ++m) dp = dp + Store<S>::ld(fin + (size_t)m * N + own);
+  }
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
     if (CZ(l) > 0 && z == 0) g[l] = -g[l] + R(2) * wall_even_dev<R>(l, dp, rho0, T0, Td, lam);
@@ -212,6 +260,16 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
+
+// e^t - 1 for the deviation form of psi (FP32 forms): the Taylor polynomial to t^6 for
+// |t| <= 1/8 (truncation below 1e-9 of the result), the exponential minus one beyond, where the
+// result is at least 0.11 in magnitude and the subtraction costs nothing beyond the rounding of
+// the exponential itself.
+__device__ __forceinline__ float expm1_dev(float t) {
+  const float p = t * (1.0f + t * (0.5f + t * (1.0f / 6.0f + t * (1.0f / 24.0f + t * (1.0f / 120.0f +
+                                                                                 t * (1.0f / 720.0f))))));
+  return fabsf(t) <= 0.125f ? p : __expf(t) - 1.0f;
+}
 
 // van der Waals-type pseudopotential psi = rho sqrt(k (a - b T_v/(1 - b rho))), k = 2/(-G)
 __device__ __forceinline__ double psi_vdw(double rho, const KPar<double>& p) {
@@ -317,6 +375,65 @@ __device__ __forceinline__ unsigned pull_index(int l, unsigned N, int z, int nz,
          (unsigned)(row[1 - CY(l)] + col[1 - CX(l)]);
 }
 
+// Local-reference storage: the reference to add to slot ls (0..18) read at element index e. For
+// ls >= 1 the reference of the slot's class (|c|^2 = 1 or 2) at the node of e, stored in slot
+// Q - 1 + |c|^2; for the rest slot the node's a0 = 12 (a1 - a2) (its index e is the node's).
+template <class S>
+__device__ __forceinline__ float loc_ref(const S* __restrict__ buf, unsigned e, int ls, unsigned N) {
+  if (ls == 0)
+    return 12.0f * (Store<S>::ld(buf + e + (unsigned)Q * N) - Store<S>::ld(buf + e + (unsigned)(Q + 1) * N));
+  return Store<S>::ld(buf + e + (unsigned)(Q - 1 + CSQ(ls) - ls) * N);
+}
+
+// The references of the populations that pull_rel reads (same addressing).
+template <class S, bool WALL>
+__device__ __forceinline__ void pull_rel_ref(float (&r)[Q], const S* __restrict__ buf, unsigned N, int pz,
+                                             int nz, unsigned own, const int (&dy)[2], const int (&dx)[2],
+                                             const unsigned (&loff)[19]) {
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const int cz = CZ(l);
+    if (WALL && ((cz > 0 && pz == 0) || (cz < 0 && pz == nz - 1))) {
+      r[l] = loc_ref<S>(buf, (unsigned)OPP(l) * N + own, OPP(l), N);
+    } else {
+      unsigned e = own + loff[l];
+      if (CY(l) > 0) e += (unsigned)dy[0];
+      if (CY(l) < 0) e += (unsigned)dy[1];
+      if (CX(l) > 0) e += (unsigned)dx[0];
+      if (CX(l) < 0) e += (unsigned)dx[1];
+      r[l] = loc_ref<S>(buf, e, l, N);
+    }
+  }
+}
+
+// The references of the populations that pull_raw reads (same addressing).
+template <class S, bool WALL>
+__device__ __forceinline__ void pull_raw_ref(float (&r)[Q], const S* __restrict__ buf, unsigned N, int pz,
+                                             int nz, unsigned plane, const int (&col)[3], const int (&row)[3]) {
+  const unsigned zb = (unsigned)pz * plane;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const int cz = CZ(l);
+    if (WALL && ((cz > 0 && pz == 0) || (cz < 0 && pz == nz - 1))) {
+      r[l] = loc_ref<S>(buf, (unsigned)OPP(l) * N + zb + (unsigned)(row[1] + col[1]), OPP(l), N);
+    } else {
+      r[l] = loc_ref<S>(buf, (unsigned)l * N + (zb - (unsigned)(cz * (int)plane)) +
+                                 (unsigned)(row[1 - CY(l)] + col[1 - CX(l)]), l, N);
+    }
+  }
+}
+
+// The two stored references of a node (rounded to the storage format) from its moment deviations:
+// f: a1 = w1 drho, a2 = w2 (4.5 dE - 0.5 drho); g: b1 = w1 dE, b2 = w2 (4.5 lam dT - 0.5 dE).
+template <class S>
+__device__ __forceinline__ void loc_refs_of(float drho, float dE, float dT, float lam, float& a1, float& a2,
+                                            float& b1, float& b2) {
+  a1 = Store<S>::rt(WT<float>(1) * drho);
+  a2 = Store<S>::rt(WT<float>(7) * (4.5f * dE - 0.5f * drho));
+  b1 = Store<S>::rt(WT<float>(1) * dE);
+  b2 = Store<S>::rt(WT<float>(7) * (4.5f * lam * dT - 0.5f * dE));
+}
+
 // 4-byte asynchronous global -> shared copy (cp.async, cached in L1 and L2); a 16-bit element is
 // copied as the aligned 4-byte word that contains it (population arrays carry 64 bytes of padding).
 template <class S>
@@ -344,6 +461,7 @@ template <> __device__ __forceinline__ double cvt<double, double>(double v) { re
 template <> __device__ __forceinline__ float cvt<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ float cvt<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <> __device__ __forceinline__ float cvt<__half, float>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float cvt<half_loc, float>(half_loc v) { return __half2float(v.h); }
 
 // Resident CTAs per SM the register allocation must allow: 512 threads per SM for the FP32 and
 // 16-bit forms (128 registers a thread); the FP64 form is limited by its shared memory anyway.
@@ -378,6 +496,11 @@ lb_fused_kernel(const KArgs a) {
   constexpr int FORCE = (VAR & VAR_GUO) ? FORCE_GUO : FORCE_SHIFT;
   constexpr bool VDW = (VAR & VAR_VDW) != 0;
   constexpr bool COLLIDE = MODE != MODE_MOMENTS, DIAG = MODE != MODE_STEP;
+  // The FP32-compute forms keep psi of the paper's pseudopotential as its deviation
+  // dpsi = psi - psi(rho0) = psi(rho0) (e^t - 1), t = 1/rho0 - 1/rho = drho/(rho rho0): the force
+  // sum of Eq. (9) (sum_l W_l c_l = 0, so dpsi may replace psi there) then adds small numbers,
+  // and its FP32 rounding is relative to the density variation, not to psi ~ 0.6.
+  constexpr bool DPSI = sizeof(typename Store<S>::R) == 4 && !VDW;
   // Code shape for the register budget: the paper's forcing takes the unswitched staging loops
   // and 64-bit store addressing (fewer instructions); the Guo-forcing variants, short of
   // registers, keep the compact forms (measured: 36-48 against 20 bytes of spills otherwise).
@@ -511,11 +634,19 @@ lb_fused_kernel(const KArgs a) {
           R f[Q];
 #pragma unroll
           for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fr[l]);
+          if constexpr (IsLoc<S>::v) {
+            float rf[Q];
+            if (wallp) pull_rel_ref<S, true>(rf, fin, N, pz, nz, zb + (unsigned)mown[i], mdy[i], mdx[i], a.loff);
+            else pull_rel_ref<S, false>(rf, fin, N, pz, nz, zb + (unsigned)mown[i], mdy[i], mdx[i], a.loff);
+#pragma unroll
+            for (int l = 0; l < Q; ++l) f[l] = f[l] + rf[l];
+          }
           R drho, jx, jy, jz;
           density_momentum<R>(f, drho, jx, jy, jz);
           const R rho = rho0 + drho;
           const R inv = rcp(rho);
           if constexpr (VDW) psi_s[s3 * RXY + k] = psi_vdw(rho, kp);
+          else if constexpr (DPSI) psi_s[s3 * RXY + k] = kp.psi0 * expm1_dev(drho * inv * kp.irho0);
           else psi_s[s3 * RXY + k] = fexp(-inv);
           if (mh[i] >= 0) {
             R* rj = rj_s + s3 * 5 * HXY + mh[i];
@@ -557,7 +688,7 @@ lb_fused_kernel(const KArgs a) {
           }
           const int h = (yr + 1) * HX + (xr + 1);
           const R rho = rj[h], inv = rj[HXY + h];
-          const R mg = -G * p0[c];
+          const R mg = -G * (DPSI ? kp.psi0 + p0[c] : p0[c]);
           const R Fx = mg * ax, Fy = mg * ay, Fz = mg * az + rho * gz;
           us[h] = (rj[2 * HXY + h] + R(0.5) * Fx) * inv;
           us[HXY + h] = (rj[3 * HXY + h] + R(0.5) * Fy) * inv;
@@ -602,6 +733,19 @@ lb_fused_kernel(const KArgs a) {
         const S* fc = fc_s + ring<D>(z) * Q * TXY + t;
 #pragma unroll
         for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fc[l * TXY]);
+        if constexpr (IsLoc<S>::v) {
+          // the references of the sources: f's and g's at the same slots of their lattices
+          float rf[Q], rg[Q];
+          if (wallz) {
+            pull_raw_ref<S, true>(rf, fin, N, z, nz, plane, ccol, crow);
+            pull_raw_ref<S, true>(rg, gin, N, z, nz, plane, ccol, crow);
+          } else {
+            pull_raw_ref<S, false>(rf, fin, N, z, nz, plane, ccol, crow);
+            pull_raw_ref<S, false>(rg, gin, N, z, nz, plane, ccol, crow);
+          }
+#pragma unroll
+          for (int l = 0; l < Q; ++l) { f[l] = f[l] + rf[l]; g[l] = g[l] + rg[l]; }
+        }
       }
       if (wallz) g_wall_fix<S, R>(g, fin, (int)N, (int)own, z, nz, rho0, T0, Td, Tu, lam);
       const int cc = (ty + 1) * HX + (tx + 1);
@@ -652,6 +796,26 @@ lb_fused_kernel(const KArgs a) {
           if constexpr (P64) return (size_t)l * NS;
           else return (size_t)((unsigned)l * N + own);
         };
+        // Local-reference storage: this node's references (of its moments at this step) go to the
+        // two reference slots, and every population slot stores its value minus the reference of
+        // its class (the readers add them back)
+        R lrf[3] = {R(0), R(0), R(0)}, lrg[3] = {R(0), R(0), R(0)};
+        if constexpr (IsLoc<S>::v) {
+          float a1, a2, b1, b2;
+          loc_refs_of<S>(drho, dE, T - T0, lam, a1, a2, b1, b2);
+          lrf[0] = 12.0f * (a1 - a2); lrf[1] = a1; lrf[2] = a2;
+          lrg[0] = 12.0f * (b1 - b2); lrg[1] = b1; lrg[2] = b2;
+          Store<S>::st(fo + sidx(Q), a1); Store<S>::st(fo + sidx(Q + 1), a2);
+          Store<S>::st(go + sidx(Q), b1); Store<S>::st(go + sidx(Q + 1), b2);
+        }
+        auto putf = [&](int l, R v) {
+          if constexpr (IsLoc<S>::v) v = v - lrf[CSQ(l)];
+          Store<S>::st(fo + sidx(l), v);
+        };
+        auto putg = [&](int l, R v) {
+          if constexpr (IsLoc<S>::v) v = v - lrg[CSQ(l)];
+          Store<S>::st(go + sidx(l), v);
+        };
         // f: BGK towards f^eq(rho, u', T), u' = (j + tau F)/rho. f^eq - fbase per class:
         // w [drho - 1.5 rho v.v + 4.5 (|c|^2-1)(dE - drho/3) + 3 rho c.v + 4.5 rho (c.v)^2]
         // (rho (T - 1/3) - rho0 (T0 - 1/3) = dE - drho/3 since rho T = E).
@@ -691,9 +855,9 @@ lb_fused_kernel(const KArgs a) {
               const R cF = R(CX(l)) * Fx + R(CY(l)) * Fy + R(CZ(l)) * Fz;
               const R ws = WT<R>(l) * ks;
               const R ssym = ws * (R(9) * cv * cF - R(3) * uF), sasym = ws * (R(3) * cF);
-              Store<S>::st(fo + sidx(l), om1 * f[l] + w * (sym + asym) + (ssym + sasym));
+              putf(l, om1 * f[l] + w * (sym + asym) + (ssym + sasym));
               if (l != 0)
-                Store<S>::st(fo + sidx(OPP(l)),
+                putf(OPP(l),
                              om1 * f[OPP(l)] + w * (sym - asym) + (ssym - sasym));
             }
           } else {
@@ -702,14 +866,14 @@ lb_fused_kernel(const KArgs a) {
             const R o0 = WT<R>(0) * om, o1 = WT<R>(1) * om, o2 = WT<R>(7) * om;
             const R wA[3] = {o0 * A[0], o1 * A[1], o2 * A[2]};
             const R q[3] = {R(0), o1 * r45, o2 * r45}, sc[3] = {R(0), o1 * r3, o2 * r3};
-            Store<S>::st(fo + sidx(0), om1 * f[0] + wA[0]);
+            putf(0, om1 * f[0] + wA[0]);
 #pragma unroll
             for (int l = 1; l < Q; l += 2) {
               const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
               const R ev = q[CLS(l)] * (cv * cv) + wA[CLS(l)];
               const R od = sc[CLS(l)] * cv;
-              Store<S>::st(fo + sidx(l), om1 * f[l] + (ev + od));
-              Store<S>::st(fo + sidx(OPP(l)), om1 * f[OPP(l)] + (ev - od));
+              putf(l, om1 * f[l] + (ev + od));
+              putf(OPP(l), om1 * f[OPP(l)] + (ev - od));
             }
           }
         }
@@ -728,14 +892,14 @@ lb_fused_kernel(const KArgs a) {
           const R k0 = WT<R>(0) * omk, k1 = WT<R>(1) * omk, k2 = WT<R>(7) * omk;
           const R P[3] = {k0 * B[0] + WT<R>(0) * Ssrc, k1 * B[1] + WT<R>(1) * Ssrc, k2 * B[2] + WT<R>(7) * Ssrc};
           const R q[3] = {R(0), k1 * e45, k2 * e45}, sc[3] = {R(0), k1 * e3, k2 * e3};
-          Store<S>::st(go + sidx(0), omk1 * g[0] + P[0]);
+          putg(0, omk1 * g[0] + P[0]);
 #pragma unroll
           for (int l = 1; l < Q; l += 2) {
             const R cu = R(CX(l)) * ux + R(CY(l)) * uy + R(CZ(l)) * uz;
             const R ev = q[CLS(l)] * (cu * cu) + P[CLS(l)];
             const R od = sc[CLS(l)] * cu;
-            Store<S>::st(go + sidx(l), omk1 * g[l] + (ev + od));
-            Store<S>::st(go + sidx(OPP(l)), omk1 * g[OPP(l)] + (ev - od));
+            putg(l, omk1 * g[l] + (ev + od));
+            putg(OPP(l), omk1 * g[OPP(l)] + (ev - od));
           }
         }
       } else {
@@ -790,6 +954,17 @@ __global__ void lb_init_kernel(const KArgs a, const double* __restrict__ rho_in,
   const R rho0 = R(a.rho0), E0 = R(a.E0), T0 = R(a.T0), lam = R(a.lam);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
     const int x = idx % nx, y = (idx / nx) % ny, z = idx / plane;
+    // local-reference storage: the node's references from its own initial fields
+    R lrf[3] = {R(0), R(0), R(0)}, lrg[3] = {R(0), R(0), R(0)};
+    if constexpr (IsLoc<S>::v) {
+      const R r = R(rho_in[idx]), T = R(T_in[idx]);
+      float a1, a2, b1, b2;
+      loc_refs_of<S>(r - rho0, r * T - E0, T - T0, lam, a1, a2, b1, b2);
+      lrf[0] = 12.0f * (a1 - a2); lrf[1] = a1; lrf[2] = a2;
+      lrg[0] = 12.0f * (b1 - b2); lrg[1] = b1; lrg[2] = b2;
+      Store<S>::st(fo + (size_t)Q * N + idx, a1); Store<S>::st(fo + (size_t)(Q + 1) * N + idx, a2);
+      Store<S>::st(go + (size_t)Q * N + idx, b1); Store<S>::st(go + (size_t)(Q + 1) * N + idx, b2);
+    }
     R fb[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
@@ -800,8 +975,8 @@ __global__ void lb_init_kernel(const KArgs a, const double* __restrict__ rho_in,
       const R r = R(rho_in[src]), T = R(T_in[src]);
       const R drho = r - rho0, dE = r * T - E0;
       const R df = WT<R>(le) * (drho + R(4.5) * (dE - drho / R(3)) * R(CSQ(le) - 1));
-      Store<S>::st(fo + (size_t)l * N + idx, df);
-      fb[l] = Store<S>::rt(df);   // the value a later load returns
+      Store<S>::st(fo + (size_t)l * N + idx, df - lrf[CSQ(l)]);
+      fb[l] = Store<S>::rt(df - lrf[CSQ(l)]) + lrf[CSQ(l)];   // the value a later pull returns
     }
     R dp = fb[0];                 // rho_p - rho0 as the step kernel forms it
 #pragma unroll
@@ -819,7 +994,7 @@ __global__ void lb_init_kernel(const KArgs a, const double* __restrict__ rho_in,
         const R Tw = (CZ(le) > 0) ? R(a.T_d) : R(a.T_u);
         dg = R(2) * wall_even_dev<R>(le, dp, rho0, T0, Tw, lam) - dg;
       }
-      Store<S>::st(go + (size_t)l * N + idx, dg);
+      Store<S>::st(go + (size_t)l * N + idx, dg - lrg[CSQ(l)]);
     }
   }
 }
@@ -840,6 +1015,18 @@ __global__ void lb_setpops_kernel(const KArgs a, const double* __restrict__ f_in
   const R rho0 = R(a.rho0), T0 = R(a.T0), lam = R(a.lam);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
     const int x = idx % nx, y = (idx / nx) % ny, z = idx / plane;
+    // local-reference storage: the node's references from the moments of the given state at it
+    R lrf[3] = {R(0), R(0), R(0)}, lrg[3] = {R(0), R(0), R(0)};
+    if constexpr (IsLoc<S>::v) {
+      double rr = 0.0, EE = 0.0;
+      for (int l = 0; l < Q; ++l) { rr += f_in[(size_t)l * N + idx]; EE += g_in[(size_t)l * N + idx]; }
+      float a1, a2, b1, b2;
+      loc_refs_of<S>(float(rr - a.rho0), float(EE - a.E0), float(EE / rr - a.T0), lam, a1, a2, b1, b2);
+      lrf[0] = 12.0f * (a1 - a2); lrf[1] = a1; lrf[2] = a2;
+      lrg[0] = 12.0f * (b1 - b2); lrg[1] = b1; lrg[2] = b2;
+      Store<S>::st(fo + (size_t)Q * N + idx, a1); Store<S>::st(fo + (size_t)(Q + 1) * N + idx, a2);
+      Store<S>::st(go + (size_t)Q * N + idx, b1); Store<S>::st(go + (size_t)(Q + 1) * N + idx, b2);
+    }
     R fb[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
@@ -848,8 +1035,8 @@ __global__ void lb_setpops_kernel(const KArgs a, const double* __restrict__ f_in
       const int src = wall ? idx : zn * plane + wrapi(y + CY(l), ny) * nx + wrapi(x + CX(l), nx);
       const int le = wall ? OPP(l) : l;   // population of the given state this slot returns
       const R df = R(f_in[(size_t)le * N + src] - a.fbase[CSQ(le)]);
-      Store<S>::st(fo + (size_t)l * N + idx, df);
-      fb[l] = Store<S>::rt(df);
+      Store<S>::st(fo + (size_t)l * N + idx, df - lrf[CSQ(l)]);
+      fb[l] = Store<S>::rt(df - lrf[CSQ(l)]) + lrf[CSQ(l)];
     }
     R dp = fb[0];
 #pragma unroll
@@ -865,7 +1052,7 @@ __global__ void lb_setpops_kernel(const KArgs a, const double* __restrict__ f_in
         const R Tw = (CZ(le) > 0) ? R(a.T_d) : R(a.T_u);
         dg = R(2) * wall_even_dev<R>(le, dp, rho0, T0, Tw, lam) - dg;
       }
-      Store<S>::st(go + (size_t)l * N + idx, dg);
+      Store<S>::st(go + (size_t)l * N + idx, dg - lrg[CSQ(l)]);
     }
   }
 }

@@ -18,9 +18,10 @@ struct PrecOps {
   cudaError_t (*info)(int by, int var, int out[4]);
   // store a given pre-collision state (float64 [19][N] f and g on the device) as the buffer
   cudaError_t (*setpops)(const KArgs&, const double*, const double*, cudaStream_t);
+  int slots;           // stored slots per lattice and node: 19, or 21 with the local references
 };
 
-extern const PrecOps kOpsF64, kOpsF32, kOpsBF16, kOpsF16;
+extern const PrecOps kOpsF64, kOpsF32, kOpsBF16, kOpsF16, kOpsF16Loc;
 
 template <class S> struct OpsImpl {
   using R = typename Store<S>::R;

@@ -5,5 +5,5 @@ namespace tlbm {
 const PrecOps kOpsF32 = {sizeof(float), 0, &OpsImpl<float>::prepare, &OpsImpl<float>::fused,
                     &OpsImpl<float>::init, &OpsImpl<float>::pops,
                     &OpsImpl<float>::tile_ok, &OpsImpl<float>::info,
-                    &OpsImpl<float>::setpops};
+                    &OpsImpl<float>::setpops, slots<float>()};
 }  // namespace tlbm

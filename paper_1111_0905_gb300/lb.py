@@ -13,9 +13,12 @@ from pathlib import Path
 
 import numpy as np
 
-LB_FP64, LB_FP32, LB_BF16_DEV, LB_FP16_DEV = 0, 1, 2, 3
-PRECISIONS = {"f64": LB_FP64, "f32": LB_FP32, "bf16dev": LB_BF16_DEV, "fp16dev": LB_FP16_DEV}
-STORAGE_BYTES = {LB_FP64: 8, LB_FP32: 4, LB_BF16_DEV: 2, LB_FP16_DEV: 2}
+LB_FP64, LB_FP32, LB_BF16_DEV, LB_FP16_DEV, LB_FP16_LOC = 0, 1, 2, 3, 4
+PRECISIONS = {"f64": LB_FP64, "f32": LB_FP32, "bf16dev": LB_BF16_DEV, "fp16dev": LB_FP16_DEV,
+              "fp16loc": LB_FP16_LOC}
+STORAGE_BYTES = {LB_FP64: 8, LB_FP32: 4, LB_BF16_DEV: 2, LB_FP16_DEV: 2, LB_FP16_LOC: 2}
+# stored values per lattice and node (the local-reference storage adds two reference slots)
+STORED_SLOTS = {LB_FP64: 19, LB_FP32: 19, LB_BF16_DEV: 19, LB_FP16_DEV: 19, LB_FP16_LOC: 21}
 LB_FORCE_SHIFT, LB_FORCE_GUO = 0, 1     # scheme variants (include/lb.h); 0 = the paper's
 LB_PSI_EXP, LB_PSI_VDW = 0, 1
 Q = 19

@@ -165,3 +165,38 @@ def test_autograd_function_matches_the_oracle_gradient(lblib, cuda, device):
     J0 = nusselt_objective(Td.detach(), Tu.detach(), G.detach(), T0.detach(), rho, w.params, nsteps, K)
     assert not J0.requires_grad
     assert abs(J0.item() - J.item()) <= 1e-12 * max(1.0, abs(J.item()))
+
+
+def test_adjoint_of_the_fp32_form_matches_its_central_differences(lblib, cuda):
+    """The 64^3 adjoint configuration in the FP32 form (FP32 forward states, FP64 reverse sweep):
+    dJ/d(T_d, T_u, G) against central differences of the FP32 form's own J within 1e-4, and a
+    random direction of dJ/dT0 within 1e-2.
+    Step sizes come from the FP32 noise floor. J of 1000 FP32 steps carries rounding noise of
+    about 1e-7 of J, which a central difference divides by 2h. Measured on this cell, the
+    difference at h = 1e-6 |p| is off by 3e-3 to 1e-2 (noise), at 1e-4 |p| by 3e-5 to 6e-5,
+    and at 1e-3 |p| by 1e-4 (truncation: the FP64 form's own difference is off by 8.7e-5 there).
+    So h = 3e-4 |p| for the scalars. For the T0 direction (unit normal entries on every node) the
+    noise is larger: at h = 1e-3 the difference is off by 3.5e-3, against 6e-5 truncation in FP64."""
+    w = config.boiling_cell(64, kappa=0.15, tau_nu=1.25)
+    p = lb.Params(**{**w.params.__dict__, "precision": lb.LB_FP32})
+    rho, T = w.fields()
+    N, K = 1000, 50
+    lat = lb.Lattice(p, rho, T)
+    got = lat.adjoint(N, K, grad_T0=True)
+    lat.close()
+    # J of the reverse sweep sums the FP64 images of the FP32 states; the forward run's J sums
+    # the same states with FP32 warp sums: equal to the FP32 rounding of the sums
+    assert abs(got["J"] - _J_gpu(p, rho, T, N)) <= 1e-6 * abs(got["J"])
+    for k in ("T_d", "T_u", "G"):
+        base = getattr(p, k)
+        h = 3e-4 * abs(base)
+        fd = (_J_gpu(lb.Params(**{**p.__dict__, k: base + h}), rho, T, N)
+              - _J_gpu(lb.Params(**{**p.__dict__, k: base - h}), rho, T, N)) / (2 * h)
+        print(f"  FP32 {k}: adjoint {got[k]:.8e}, central difference {fd:.8e} ({fd / got[k] - 1:+.2e})")
+        assert abs(fd - got[k]) <= 1e-4 * abs(fd), (k, fd, got[k])
+    v = np.random.default_rng(64).standard_normal(T.shape)
+    h = 1e-3
+    fd = (_J_gpu(p, rho, T + h * v, N) - _J_gpu(p, rho, T - h * v, N)) / (2 * h)
+    ad = float((got["T0"] * v).sum())
+    print(f"  FP32 T0 direction: adjoint {ad:.8e}, central difference {fd:.8e} ({fd / ad - 1:+.2e})")
+    assert abs(fd - ad) <= 1e-2 * abs(fd), (fd, ad)

@@ -6,8 +6,9 @@ the corners, nodes on both walls and next to them, on the x/y tile seams and on 
 seams, and seeded random nodes.
 
 Cells: the 128^3 single-phase cell in FP32 (the benchmark's headline form); the 256^3 boiling
-cell in BF16 and FP16 deviation storage; the 512^3 boiling cell in FP32 and FP16 deviation
-storage (the sizes the bandwidth figures are quoted at). Tolerances as for the small grids: FP32
+cell in BF16 and FP16 deviation storage and FP16 against local references; the 512^3 boiling
+cell in FP32, FP16 deviation storage and FP16 against local references (the sizes the bandwidth
+figures are quoted at). Tolerances as for the small grids: FP32
 1e-5 of each field's scale (u on a floor of 1e-2), 16-bit 2e-3 on rho and T.
 """
 import numpy as np
@@ -64,12 +65,12 @@ def test_fp32_single_phase_128(lblib, cuda):
     _check(config.single_phase_cell(128, precision=lb.LB_FP32), 1e-5, 1e-5, 128)
 
 
-@pytest.mark.parametrize("prec", [lb.LB_BF16_DEV, lb.LB_FP16_DEV])
+@pytest.mark.parametrize("prec", [lb.LB_BF16_DEV, lb.LB_FP16_DEV, lb.LB_FP16_LOC])
 def test_16bit_boiling_256(lblib, cuda, prec):
     _check(config.paper_scale_cell(256, precision=prec), 2e-3, None, 256 + prec)
 
 
-@pytest.mark.parametrize("prec,tol", [(lb.LB_FP32, 1e-5), (lb.LB_FP16_DEV, 2e-3)])
+@pytest.mark.parametrize("prec,tol", [(lb.LB_FP32, 1e-5), (lb.LB_FP16_DEV, 2e-3), (lb.LB_FP16_LOC, 2e-3)])
 def test_boiling_512(lblib, cuda, prec, tol):
     _check(config.paper_scale_cell(512, precision=prec), tol, 1e-5 if prec == lb.LB_FP32 else None,
            512 + prec)

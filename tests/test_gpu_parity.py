@@ -134,7 +134,7 @@ def test_fp32_boiling_parity(lblib, cuda):
     print("FP32 boiling errors:", errs)
 
 
-@pytest.mark.parametrize("prec", [lb.LB_BF16_DEV, lb.LB_FP16_DEV])
+@pytest.mark.parametrize("prec", [lb.LB_BF16_DEV, lb.LB_FP16_DEV, lb.LB_FP16_LOC])
 def test_16bit_deviation_storage(lblib, cuda, prec):
     """rho and T within 2e-3 of the FP64 oracle after 50 steps of the single-phase cell."""
     w = config.single_phase_cell(32, precision=prec)
@@ -243,10 +243,11 @@ def test_device_pointers_and_stream(lblib, cuda):
 
 
 SHAPES = [(8, 0), (8, 5), (8, 23), (4, 7), (4, 1), (16, 23), (16, 3)]
-CROSS_TILE_TOL = {lb.LB_FP64: 1e-12, lb.LB_FP32: 1e-5, lb.LB_BF16_DEV: 2e-3, lb.LB_FP16_DEV: 2e-3}
+CROSS_TILE_TOL = {lb.LB_FP64: 1e-12, lb.LB_FP32: 1e-5, lb.LB_BF16_DEV: 2e-3, lb.LB_FP16_DEV: 2e-3,
+                  lb.LB_FP16_LOC: 2e-3}
 
 
-@pytest.mark.parametrize("prec", [lb.LB_FP64, lb.LB_FP32, lb.LB_BF16_DEV, lb.LB_FP16_DEV])
+@pytest.mark.parametrize("prec", [lb.LB_FP64, lb.LB_FP32, lb.LB_BF16_DEV, lb.LB_FP16_DEV, lb.LB_FP16_LOC])
 def test_launch_shape_does_not_change_the_result(lblib, cuda, prec):
     """Chunk prologues recompute their planes with the same arithmetic: for one tile height the
     populations after 30 steps of a ragged boiling cell are bitwise equal whatever the z chunk.
@@ -541,15 +542,16 @@ def _fp32_from(p, rho, T, f, g, steps):
 
 
 def test_fp32_parity_on_a_convecting_state(lblib, cuda):
-    """FP32 form against the oracle from developed convection, element by element at the FP32
-    tolerance of 1e-5 relative with no velocity floor: the 128^3 single-phase cell after 2000 FP64
-    GPU steps (Nu about 1.67), then 10 steps of each. rho, T, every velocity component on the
-    largest |u|, and Nu(z) on the scale of its convective term <|rho U u_z|>/(kappa dT/nz)."""
-    w = config.single_phase_cell(128)
+    """FP32 form against the oracle from a flowing state, element by element at the FP32
+    tolerance of 1e-5 relative with no velocity floor: the 96^3 single-phase cell after 1000 FP64
+    GPU steps (the buoyancy-driven adjustment of the initial state, |u| up to 6e-3), then 10 steps
+    of each. rho, T, every velocity component on the largest |u|, and Nu(z) on the scale of its
+    convective term <|rho U u_z|>/(kappa dT/nz)."""
+    w = config.single_phase_cell(96)
     p = w.params
     rho, T = w.fields()
     lat = lb.Lattice(p, rho, T)
-    lat.step(2000)
+    lat.step(1000)
     f, g = lat.populations()
     lat.close()
     errs = _fp32_from(p, rho, T, f, g, 10)
@@ -596,3 +598,57 @@ def test_checkpoint_of_other_physics_parameters_is_refused(lblib, cuda, tmp_path
     b.load(tmp_path / "a.bin")
     assert b.step_count == 3
     b.close()
+
+
+def test_fp16_local_references_against_the_oracle(lblib, cuda):
+    """FP16 storage against local references on the boiling cell (phase separation, ragged tiles,
+    several z chunks): rho, T and the populations within 2e-3 of the oracle after 30 steps, and
+    Nu(z) within 2e-3 of its convective scale. Its rounding is of the non-equilibrium and
+    velocity parts only, so it also stays within 1e-4 here (FP16 deviations from the global
+    reference: ~1e-3)."""
+    w = config.boiling_cell(40, nz=11, ny=19, precision=lb.LB_FP16_LOC)
+    p = w.params
+    p.tile_y, p.z_chunk = 8, 4
+    rho, T = w.fields()
+    lat = lb.Lattice(p, rho, T)
+    lat.step(30)
+    r, u, TT = lat.moments()
+    f_g, g_g = lat.populations()
+    nu = lat.nusselt()[1]
+    lat.close()
+    f, g, op, _ = oracle_run(p, rho, T, 30)
+    r_o, u_o, T_o = lbm.moments_out(f, g, op)
+    errs = {"rho": rel_err(r, r_o), "T": rel_err(TT, T_o), "f": rel_err(f_g, f), "g": rel_err(g_g, g),
+            "nu_on_conv": float(np.abs(nu - lbm.nusselt(f, g, op)[1].numpy()).max()) / _conv_scale(f, g, op)}
+    print("FP16 local-reference errors:", errs)
+    assert max(errs["rho"], errs["T"], errs["f"], errs["g"]) < 1e-4, errs
+    assert errs["nu_on_conv"] < 2e-3, errs
+
+
+@pytest.mark.parametrize("prec", [lb.LB_FP16_LOC, lb.LB_FP32])
+def test_set_populations_and_checkpoints_carry_the_references(lblib, cuda, prec, tmp_path):
+    """With the local-reference storage the two reference slots are part of the state: a
+    checkpoint round trip continues bitwise, and lb_set_populations of an exported state
+    continues within the storage's rounding."""
+    w = config.boiling_cell(20, nz=12, ny=10, precision=prec)
+    rho, T = w.fields()
+    a = lb.Lattice(w.params, rho, T)
+    a.step(15)
+    a.save(tmp_path / "c.bin")
+    f, g = a.populations()
+    a.step(10)
+    fa, ga = a.populations()
+    b = lb.Lattice(w.params, rho, T)
+    b.load(tmp_path / "c.bin")
+    b.step(10)
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    c = lb.Lattice(w.params, rho, T)
+    c.set_populations(f, g)
+    f1, g1 = c.populations()
+    tol = 1e-6 if prec == lb.LB_FP32 else 2e-4
+    assert rel_err(f1, f) < tol and rel_err(g1, g) < tol, (rel_err(f1, f), rel_err(g1, g))
+    c.step(10)
+    fc, gc = c.populations()
+    assert rel_err(fc, fa) < 10 * tol and rel_err(gc, ga) < 10 * tol
+    a.close(); b.close(); c.close()
