@@ -222,9 +222,10 @@ __global__ void __launch_bounds__(256) coll_adj_kernel(const double* __restrict_
     const double a_D = lS * (-E / p.cv);
     // Nu terms: J_n = (1/N_t)[1 + sum_x rho U u_z / (kappa (T_d - T_u) nx ny)], U = c_v T + (G/4) e^{-2/rho}
     if (p.include_nu) {
-      const double e2 = exp(-2.0 / rho);
+      const double psi = M[MF_PSI * N + i];
+      const double e2 = psi * psi;            // e^{-2/rho} = psi^2
       const double U = p.cv * T + 0.25 * p.G * e2;
-      a_rho += p.Kc * (U * uz + rho * uz * 0.5 * p.G * e2 / (rho * rho));
+      a_rho += p.Kc * (U * uz + uz * 0.5 * p.G * e2 / rho);
       a_T += p.Kc * rho * p.cv * uz;
       a_u[2] += p.Kc * rho * U;
       pG += p.Kc * rho * uz * 0.25 * e2;
@@ -259,13 +260,13 @@ __global__ void vel_adj_kernel(const double* __restrict__ M, Geom g, Par p, doub
     const double dm = (z >= 1) ? A[AF_D * N + i - g.plane] : A[AF_D * N + i];
     const double dp = (z <= g.nz - 2) ? A[AF_D * N + i + g.plane] : A[AF_D * N + i];
     lu[2] += 0.5 * (dm - dp);
-    const double rho = M[MF_RHO * N + i];
+    const double inv = 1.0 / M[MF_RHO * N + i];   // one division per node on the FP64 pipe
     double a_rho = A[AF_RHO * N + i];
     for (int a = 0; a < 3; ++a) {
       const double lv = A[(AF_VX + a) * N + i];
-      A[(AF_JX + a) * N + i] = (lv + lu[a]) / rho;
-      A[(AF_FX + a) * N + i] = (p.tau * lv + 0.5 * lu[a]) / rho;
-      a_rho -= (M[(MF_VX + a) * N + i] * lv + M[(MF_UX + a) * N + i] * lu[a]) / rho;
+      A[(AF_JX + a) * N + i] = (lv + lu[a]) * inv;
+      A[(AF_FX + a) * N + i] = (p.tau * lv + 0.5 * lu[a]) * inv;
+      a_rho -= (M[(MF_VX + a) * N + i] * lv + M[(MF_UX + a) * N + i] * lu[a]) * inv;
     }
     A[AF_RHO * N + i] = a_rho;
   }
@@ -303,10 +304,11 @@ __global__ void force_adj_kernel(const double* __restrict__ M, Geom g, Par p,
         lpsi += -p.G * W * cl * M[MF_PSI * N + j];
       }
     }
-    double a_rho = A[AF_RHO * N + i] + p.gz * lF[2] + lpsi * psi / (rho * rho);
+    const double inv = 1.0 / rho;
+    double a_rho = A[AF_RHO * N + i] + p.gz * lF[2] + lpsi * psi * inv * inv;
     const double a_T = A[AF_T * N + i];
-    const double a_E = a_T / rho;
-    a_rho -= a_T * T / rho;
+    const double a_E = a_T * inv;
+    a_rho -= a_T * T * inv;
     const double lj[3] = {A[AF_JX * N + i], A[AF_JY * N + i], A[AF_JZ * N + i]};
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
