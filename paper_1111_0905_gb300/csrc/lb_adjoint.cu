@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(256) coll_adj_kernel(const double* __restrict_
     double sfk = 0.0, sf = 0.0, sg = 0.0;          // sums of s_f k, s_f and s_g over the pairs
     double avx = 0.0, avy = 0.0, avz = 0.0, aux = 0.0, auy = 0.0, auz = 0.0;
     const double Tm = 4.5 * (T - 1.0 / 3.0), lk = 4.5 * (p.lam - rho / 3.0);
+    const double ev0 = 1.0 - 1.5 * vv, eu0 = 1.0 - 1.5 * uu;   // the velocity-squared parts
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       if (l != 0 && (l & 1) == 0) continue;    // with its odd partner
@@ -191,27 +192,43 @@ __global__ void __launch_bounds__(256) coll_adj_kernel(const double* __restrict_
         L[o * N + i] = (1.0 - p.om) * lfo;
         L[(Q + o) * N + i] = (1.0 - p.omk) * lgo;
       }
-      const double k = CSQ(l) - 1, w = WT<double>(l);
-      const double cv = CX(l) * vx + CY(l) * vy + CZ(l) * vz;
-      const double cu = CX(l) * ux + CY(l) * uy + CZ(l) * uz;
-      const double af = p.om * w * lf, afo = p.om * w * lfo;
-      const double ag = p.omk * w * lg, ago = p.omk * w * lgo;
-      const double s_f = af + afo, d_f = af - afo, s_g = ag + ago, d_g = ag - ago;
+      // class factor k = |c_l|^2 - 1 (-1 rest, 0 axis, +1 diagonal) taken by branches that fold,
+      // so that no multiply by k is executed
+      const int kc = CSQ(l) - 1;
+      const double w = WT<double>(l);
+      const double af = p.om * w * lf, ag = p.omk * w * lg;
       // f^eq: even 1 + 4.5 (c.v)^2 - 1.5 v.v + 4.5 (T - 1/3) k, odd 3 c.v; d/dT 4.5 k rho;
       // d/dv rho (3 c + 9 (c.v) c - 3 v)
-      a_rho += s_f * (1.0 + 4.5 * cv * cv - 1.5 * vv + Tm * k) + d_f * (3.0 * cv);
-      sfk += s_f * k;
-      sf += s_f;
-      const double ef = 3.0 * d_f + 9.0 * s_f * cv;
-      avx += ef * CX(l); avy += ef * CY(l); avz += ef * CZ(l);
       // g^eq: rho T P(u) + 4.5 (lam T - rho T/3) k, P even 1 + 4.5 (c.u)^2 - 1.5 u.u, odd 3 c.u
-      const double Pe = 1.0 + 4.5 * cu * cu - 1.5 * uu, Po = 3.0 * cu;
-      a_rho += T * (s_g * (Pe - 1.5 * k) + d_g * Po);
-      a_T += rho * (s_g * Pe + d_g * Po) + s_g * lk * k;
-      sg += s_g;
-      const double eg = 3.0 * d_g + 9.0 * s_g * cu;
-      aux += eg * CX(l); auy += eg * CY(l); auz += eg * CZ(l);
-      lS += w * (lg + lgo);
+      if (l == 0) {
+        // the rest population (c = 0, k = -1): even parts only
+        a_rho += af * (ev0 - Tm) + T * (ag * (eu0 + 1.5));
+        a_T += rho * (ag * eu0) - ag * lk;
+        sfk -= af;
+        sf += af;
+        sg += ag;
+        lS += w * lg;
+      } else {
+        const double cv = cdot<double>(l, vx, vy, vz);
+        const double cu = cdot<double>(l, ux, uy, uz);
+        const double afo = p.om * w * lfo, ago = p.omk * w * lgo;
+        const double s_f = af + afo, d_f = af - afo, s_g = ag + ago, d_g = ag - ago;
+        const double evf = kc == 0 ? ev0 : ev0 + Tm;          // axis: k = 0, diagonal: k = 1
+        a_rho += s_f * (evf + 4.5 * cv * cv) + d_f * (3.0 * cv);
+        if (kc != 0) sfk += s_f;
+        sf += s_f;
+        const double ef = 3.0 * d_f + 9.0 * s_f * cv;
+        cadd<double>(l, ef, avx, avy, avz);
+        const double Pe = eu0 + 4.5 * cu * cu, Po = 3.0 * cu;
+        const double Pk = kc == 0 ? Pe : Pe - 1.5;
+        a_rho += T * (s_g * Pk + d_g * Po);
+        a_T += rho * (s_g * Pe + d_g * Po);
+        if (kc != 0) a_T += s_g * lk;
+        sg += s_g;
+        const double eg = 3.0 * d_g + 9.0 * s_g * cu;
+        cadd<double>(l, eg, aux, auy, auz);
+        lS += w * (lg + lgo);
+      }
     }
     a_T += 4.5 * rho * sfk;
     double a_v[3] = {rho * (avx - 3.0 * vx * sf), rho * (avy - 3.0 * vy * sf), rho * (avz - 3.0 * vz * sf)};
@@ -272,6 +289,14 @@ __global__ void vel_adj_kernel(const double* __restrict__ M, Geom g, Par p, doub
   }
 }
 
+// c_l . (lambda_Fx, lambda_Fy, lambda_Fz) at node j, loading only the components c_l has
+__device__ __forceinline__ double cdot_at(int l, const double* __restrict__ A, size_t N, int j) {
+  const double x = CX(l) != 0 ? A[AF_FX * N + j] : 0.0;
+  const double y = CY(l) != 0 ? A[AF_FY * N + j] : 0.0;
+  const double z = CZ(l) != 0 ? A[AF_FZ * N + j] : 0.0;
+  return cdot<double>(l, x, y, z);
+}
+
 // force^T (psi gather with mirrored ghosts), psi^T, T = E/rho ^T and moments^T
 __global__ void force_adj_kernel(const double* __restrict__ M, Geom g, Par p,
                                  const double* __restrict__ A, double* __restrict__ L,
@@ -294,13 +319,13 @@ __global__ void force_adj_kernel(const double* __restrict__ M, Geom g, Par p,
       const int zi = z - CZ(l);          // interior link x = y - c_l
       if (zi >= 0 && zi < g.nz) {
         const int j = at(g, x - CX(l), y - CY(l), zi);
-        const double cl = CX(l) * A[AF_FX * N + j] + CY(l) * A[AF_FY * N + j] + CZ(l) * A[AF_FZ * N + j];
+        const double cl = cdot_at(l, A, N, j);
         lpsi += -p.G * W * cl * M[MF_PSI * N + j];
       }
       const int zg = z + CZ(l);          // ghost link: x in this plane, x + c_l beyond a wall
       if (CZ(l) != 0 && (zg < 0 || zg >= g.nz)) {
         const int j = at(g, x - CX(l), y - CY(l), z);
-        const double cl = CX(l) * A[AF_FX * N + j] + CY(l) * A[AF_FY * N + j] + CZ(l) * A[AF_FZ * N + j];
+        const double cl = cdot_at(l, A, N, j);
         lpsi += -p.G * W * cl * M[MF_PSI * N + j];
       }
     }
@@ -312,7 +337,7 @@ __global__ void force_adj_kernel(const double* __restrict__ M, Geom g, Par p,
     const double lj[3] = {A[AF_JX * N + i], A[AF_JY * N + i], A[AF_JZ * N + i]};
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      L[l * N + i] += a_rho + CX(l) * lj[0] + CY(l) * lj[1] + CZ(l) * lj[2];
+      L[l * N + i] += (l == 0) ? a_rho : a_rho + cdot<double>(l, lj[0], lj[1], lj[2]);
       L[(Q + l) * N + i] += a_E;
     }
   }

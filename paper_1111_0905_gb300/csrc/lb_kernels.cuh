@@ -193,6 +193,35 @@ __device__ __forceinline__ void pull(R (&v)[Q], const S* __restrict__ buf, int N
   }
 }
 
+// c_l . (x, y, z) from the nonzero components of c_l only (with l a compile-time constant the
+// branches fold away). Written as R(c) * x + ..., an IEEE multiply by a zero component (and the
+// add of its +-0) would still be executed: 0 * x cannot be folded (x may be a NaN or infinite).
+template <class R>
+__device__ __forceinline__ R cdot(int l, R x, R y, R z) {
+  const int cx = CX(l), cy = CY(l), cz = CZ(l);
+  R s;
+  if (cx != 0) {
+    s = cx > 0 ? x : -x;
+    if (cy != 0) s = cy > 0 ? s + y : s - y;
+    if (cz != 0) s = cz > 0 ? s + z : s - z;
+  } else if (cy != 0) {
+    s = cy > 0 ? y : -y;
+    if (cz != 0) s = cz > 0 ? s + z : s - z;
+  } else if (cz != 0) {
+    s = cz > 0 ? z : -z;
+  } else {
+    s = R(0);
+  }
+  return s;
+}
+// a += c_la v for the nonzero components c_la of c_l (a = (ax, ay, az))
+template <class R>
+__device__ __forceinline__ void cadd(int l, R v, R& ax, R& ay, R& az) {
+  if (CX(l) != 0) ax = CX(l) > 0 ? ax + v : ax - v;
+  if (CY(l) != 0) ay = CY(l) > 0 ? ay + v : ay - v;
+  if (CZ(l) != 0) az = CZ(l) > 0 ? az + v : az - v;
+}
+
 // class of direction l: 0 rest, 1 axis, 2 diagonal (= |c_l|^2)
 __host__ __device__ constexpr int CLS(int l) { return CSQ(l); }
 
@@ -848,11 +877,11 @@ lb_fused_kernel(const KArgs a) {
 #pragma unroll
             for (int l = 0; l < Q; ++l) {
               if (l != 0 && (l & 1) == 0) continue;     // handled with its odd partner
-              const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
+              const R cv = cdot<R>(l, vx, vy, vz);
               const R w = WT<R>(l) * om;
               const R sym = A[CLS(l)] + r45 * cv * cv;
               const R asym = r3 * cv;
-              const R cF = R(CX(l)) * Fx + R(CY(l)) * Fy + R(CZ(l)) * Fz;
+              const R cF = cdot<R>(l, Fx, Fy, Fz);
               const R ws = WT<R>(l) * ks;
               const R ssym = ws * (R(9) * cv * cF - R(3) * uF), sasym = ws * (R(3) * cF);
               putf(l, om1 * f[l] + w * (sym + asym) + (ssym + sasym));
@@ -869,7 +898,7 @@ lb_fused_kernel(const KArgs a) {
             putf(0, om1 * f[0] + wA[0]);
 #pragma unroll
             for (int l = 1; l < Q; l += 2) {
-              const R cv = R(CX(l)) * vx + R(CY(l)) * vy + R(CZ(l)) * vz;
+              const R cv = cdot<R>(l, vx, vy, vz);
               const R ev = q[CLS(l)] * (cv * cv) + wA[CLS(l)];
               const R od = sc[CLS(l)] * cv;
               putf(l, om1 * f[l] + (ev + od));
@@ -895,7 +924,7 @@ lb_fused_kernel(const KArgs a) {
           putg(0, omk1 * g[0] + P[0]);
 #pragma unroll
           for (int l = 1; l < Q; l += 2) {
-            const R cu = R(CX(l)) * ux + R(CY(l)) * uy + R(CZ(l)) * uz;
+            const R cu = cdot<R>(l, ux, uy, uz);
             const R ev = q[CLS(l)] * (cu * cu) + P[CLS(l)];
             const R od = sc[CLS(l)] * cu;
             putg(l, omk1 * g[l] + (ev + od));
