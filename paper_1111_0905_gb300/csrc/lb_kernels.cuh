@@ -214,6 +214,13 @@ __device__ __forceinline__ R cdot(int l, R x, R y, R z) {
   }
   return s;
 }
+// c_l . (x, y, z) in the step kernel of storage S: from the nonzero components, except for the
+// FP32 kernel, where the plain multiply form measured 0.6-1.0 % faster (its code schedules better)
+template <class S, class R>
+__device__ __forceinline__ R cdot_s(int l, R x, R y, R z) {
+  if constexpr (std::is_same<S, float>::value) return R(CX(l)) * x + R(CY(l)) * y + R(CZ(l)) * z;
+  else return cdot<R>(l, x, y, z);
+}
 // a += c_la v for the nonzero components c_la of c_l (a = (ax, ay, az))
 template <class R>
 __device__ __forceinline__ void cadd(int l, R v, R& ax, R& ay, R& az) {
@@ -877,11 +884,11 @@ lb_fused_kernel(const KArgs a) {
 #pragma unroll
             for (int l = 0; l < Q; ++l) {
               if (l != 0 && (l & 1) == 0) continue;     // handled with its odd partner
-              const R cv = cdot<R>(l, vx, vy, vz);
+              const R cv = cdot_s<S, R>(l, vx, vy, vz);
               const R w = WT<R>(l) * om;
               const R sym = A[CLS(l)] + r45 * cv * cv;
               const R asym = r3 * cv;
-              const R cF = cdot<R>(l, Fx, Fy, Fz);
+              const R cF = cdot_s<S, R>(l, Fx, Fy, Fz);
               const R ws = WT<R>(l) * ks;
               const R ssym = ws * (R(9) * cv * cF - R(3) * uF), sasym = ws * (R(3) * cF);
               putf(l, om1 * f[l] + w * (sym + asym) + (ssym + sasym));
@@ -898,7 +905,7 @@ lb_fused_kernel(const KArgs a) {
             putf(0, om1 * f[0] + wA[0]);
 #pragma unroll
             for (int l = 1; l < Q; l += 2) {
-              const R cv = cdot<R>(l, vx, vy, vz);
+              const R cv = cdot_s<S, R>(l, vx, vy, vz);
               const R ev = q[CLS(l)] * (cv * cv) + wA[CLS(l)];
               const R od = sc[CLS(l)] * cv;
               putf(l, om1 * f[l] + (ev + od));
@@ -924,7 +931,7 @@ lb_fused_kernel(const KArgs a) {
           putg(0, omk1 * g[0] + P[0]);
 #pragma unroll
           for (int l = 1; l < Q; l += 2) {
-            const R cu = cdot<R>(l, ux, uy, uz);
+            const R cu = cdot_s<S, R>(l, ux, uy, uz);
             const R ev = q[CLS(l)] * (cu * cu) + P[CLS(l)];
             const R od = sc[CLS(l)] * cu;
             putg(l, omk1 * g[l] + (ev + od));
