@@ -47,18 +47,18 @@ KERNEL_TYPE = {"f64": "double", "f32": "float", "bf16dev": "__nv_bfloat16", "fp1
 # launch time is kept to a few GB on the device), keyed by the hash of the kernel sources it
 # was taken on. The headline's traffic is that capture scaled by the node count (the traffic
 # of one launch grows in proportion to the nodes it updates); null once the sources changed.
-TRAFFIC = {"src_hash": "4dc33a88eefcb674", "nodes": 192 ** 3,
-           "bytes_per_launch": {"f32": 1146192640 + 1031474688, "fp16loc": 601407744 + 553471488,
-                                "fp16dev": 543572480 + 495181312},
+TRAFFIC = {"src_hash": "1c0c78cec5500b38", "nodes": 192 ** 3,
+           "bytes_per_launch": {"f32": 1145270784 + 1032354304, "fp16loc": 601441280 + 553468160,
+                                "fp16dev": 543643648 + 495129856},
            "what": "ncu DRAM bytes of one launch of the 192^3 paper-geometry cell, scaled by the node count"}
 
 # FP64 operations per node of the FP64 step kernel (ncu: 2 x DFMA + DADD + DMUL thread
-# instructions of one launch of the 128^3 single-phase cell, 2 x 429,355,008 + 241,653,760 +
-# 129,112,064, divided by its 2,097,152 nodes; this counts the ring recomputation, i.e. the work
+# instructions of one launch of the 128^3 single-phase cell, 2 x 395,800,576 + 241,686,528 +
+# 116,529,152, divided by its 2,097,152 nodes; this counts the ring recomputation, i.e. the work
 # the kernel issues, and slightly overstates 512^3, whose chunk prologues are a smaller share),
 # and GB300's nominal FP64 rate (152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz = 1.26
 # TFLOP/s; no measured FP64 peak).
-FP64_FLOPS_PER_NODE = (2 * 429355008 + 241653760 + 129112064) / 2097152
+FP64_FLOPS_PER_NODE = (2 * 395800576 + 241686528 + 116529152) / 2097152
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
