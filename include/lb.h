@@ -59,8 +59,9 @@ typedef enum {
  * scale): float32 stays within 1e-6 on rho and T over 2000 single-phase steps and 5e-5 over 5000
  * boiling steps of the 256^3 cell; float16 deviations within 2e-3 over 2000 single-phase steps but
  * not over long boiling runs (4e-2 after 5000 steps: the phase pattern drifts); bfloat16 deviations
- * only over short runs (a few hundred steps); float16 against local references within 2e-3 over
- * both horizons. */
+ * only over a few tens of steps (within 2e-3 after 50 steps of a 32^3 cell, 3.8e-3 after 100 steps
+ * of the 512^3 boiling cell); float16 against local references within 2e-3 over both horizons
+ * (2.3e-4 after 5000 boiling steps of the 256^3 cell). */
 
 /* Scheme variants for comparison with the paper's scheme (variant 0 of each; the paper defines
  * neither alternative). Forcing: LB_FORCE_SHIFT, the paper's equilibrium velocity
