@@ -342,9 +342,11 @@ def test_variant_parity_fp32(lblib, cuda, forcing, psi):
     _compare(p, rho, T, 15, 1e-5, nu_tol=1e-5)
 
 
-def test_variant_parity_16bit(lblib, cuda):
-    """Guo forcing with the van der Waals psi in FP16 deviation storage: rho and T within 2e-3."""
-    p, rho, T = _variant_cell(lb.LB_FORCE_GUO, lb.LB_PSI_VDW, lb.LB_FP16_DEV)
+@pytest.mark.parametrize("prec", [lb.LB_FP16_DEV, lb.LB_FP16_LOC])
+def test_variant_parity_16bit(lblib, cuda, prec):
+    """Guo forcing with the van der Waals psi in FP16 storage (deviations, and against local
+    references): rho and T within 2e-3."""
+    p, rho, T = _variant_cell(lb.LB_FORCE_GUO, lb.LB_PSI_VDW, prec)
     lat = lb.Lattice(p, rho, T)
     lat.step(15)
     r, u, TT = lat.moments()
@@ -378,7 +380,8 @@ def test_variant_arguments(lblib, cuda):
     lat.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(lb.LB_FP64, 1e-12), (lb.LB_FP32, 1e-6), (lb.LB_FP16_DEV, 1e-6)])
+@pytest.mark.parametrize("prec,tol", [(lb.LB_FP64, 1e-12), (lb.LB_FP32, 1e-6), (lb.LB_FP16_DEV, 1e-6),
+                                      (lb.LB_FP16_LOC, 1e-6)])
 def test_fused_nu_samples_equal_separate_passes(lblib, cuda, prec, tol):
     """With nu_every the Nu sample of state n is taken by the launch of step n -> n+1 (fused); the
     time average equals the mean of lb_nusselt called after every step (separate moments
