@@ -39,6 +39,9 @@ STORE_BYTES = {"f64": 8, "f32": 4, "bf16dev": 2, "fp16dev": 2, "fp16loc": 2}
 # values stored per lattice and node: the 19 populations, plus two reference slots for the FP16
 # storage against local references (its extra traffic counts against its roofline fraction)
 STORED_SLOTS = {"f64": 19, "f32": 19, "bf16dev": 19, "fp16dev": 19, "fp16loc": 21}
+# forms whose traffic is the 76 values per node of the yardstick lb_stream_bound (the FP64 form is
+# bound by its FP64 pipe; the local-reference form also loads the source nodes' references)
+PATTERN_FORMS = ("f32", "fp16dev", "bf16dev")
 KERNEL_TYPE = {"f64": "double", "f32": "float", "bf16dev": "__nv_bfloat16", "fp16dev": "__half",
                "fp16loc": "tlbm::half_loc"}
 
@@ -291,9 +294,17 @@ def run_ours(args):
                          "launch": launch}
         torch.cuda.empty_cache()
 
+    # the bound of the access pattern itself: the step's loads and stores without its arithmetic
+    pattern = stream_bound_sweep(lb, torch, peaks, p0, results[main_form]["launch"]["ctas_per_sm"])
+    for form in results:
+        b = pattern.get(f"{STORE_BYTES[form]}B") if form in PATTERN_FORMS else None
+        if b is not None:
+            results[form]["frac_of_pattern_bound"] = results[form]["hbm_gbs_algorithmic"] / b["same_residency"]["GBs"]
+
     if args.only:
         if rank == 0:
-            print(json.dumps({"only": args.only, "n": n, "form": results[args.only]}))
+            print(json.dumps({"only": args.only, "n": n, "form": results[args.only],
+                              "pattern_bound": pattern}))
         if ws > 1:
             dist.destroy_process_group()
         return None
@@ -391,6 +402,14 @@ def run_ours(args):
                 "kernel": f"tlbm::lb_fused_kernel<{KERNEL_TYPE[main_form]},8,0,0>",
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "algorithmic": f"76 values x {STORE_BYTES[main_form]} B x {N} nodes (19 f + 19 g read and written)"}
+    pb = pattern.get(f"{STORE_BYTES[main_form]}B") if main_form in PATTERN_FORMS else None
+    if pb is not None:
+        same = pb["same_residency"]
+        roofline["pattern_bound"] = {
+            "GBs": same["GBs"], "frac_of_peak": same["frac_of_peak"], "warps_per_sm": same["warps_per_sm"],
+            "frac_achieved_of_it": roofline["achieved"] / same["GBs"],
+            "what": "lb_stream_bound (the step's 76 loads and stores per node, no arithmetic) timed live "
+                    "at the fused kernel's resident warps per SM"}
 
     out = None
     if rank == 0:
@@ -407,6 +426,45 @@ def run_ours(args):
         print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
+    return out
+
+
+def stream_bound_sweep(lb, torch, peaks, p, fused_ctas: int) -> dict:
+    """lb_stream_bound on the cell's grid in 4- and 2-byte elements: at the fused kernel's residency
+    (its CTAs per SM, 256 threads each like the fused kernel's), at the yardstick's own occupancy
+    limit, and one node per thread. 76 values per node per launch; inputs far larger than L2 and
+    alternated between two pairs of lattices."""
+    shape = (p.nz, p.ny, p.nx)
+    N = p.nx * p.ny * p.nz
+    st = torch.cuda.current_stream()
+    out = {}
+    for elem, dt in ((4, torch.float32), (2, torch.float16)):
+        bufs = [torch.zeros(Q * N, dtype=dt, device="cuda") for _ in range(4)]
+        occ = lb.stream_bound(*bufs, shape, 0)
+        res = {}
+        for name, ctas in (("same_residency", min(fused_ctas, occ)), ("occupancy_limit", occ),
+                           ("node_per_thread", 0)):
+            def launch(k):
+                a, b = (0, 2) if k % 2 == 0 else (2, 0)
+                lb.stream_bound(bufs[a], bufs[a + 1], bufs[b], bufs[b + 1], shape, ctas)
+            for k in range(3):
+                launch(k)
+            K = 10
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for k in range(K):
+                launch(k)
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            gbs = 4 * Q * elem * N / (ms * 1e-3) / 1e9
+            res[name] = {"ctas_per_sm": ctas, "warps_per_sm": 8 * ctas if ctas else None, "ms": ms,
+                         "GBs": gbs, "frac_of_peak": gbs / peaks["hbm_gbs"]}
+        out[f"{elem}B"] = res
+        del bufs
+        torch.cuda.empty_cache()
     return out
 
 
@@ -478,10 +536,11 @@ def diagnostics_cost(lb, torch, max_over_ranks, barrier, sizes) -> dict:
 
 
 def adjoint_cost(lb, torch) -> dict:
-    """The discrete adjoint on the 64^3 boiling cell (FP64, 1000 steps, checkpoints every 50):
-    wall time of lb_adjoint_step (J and dJ/d(T_d, T_u, G)) against (a) the plain forward run,
-    lb_step(1000) with no Nu sampling, and (b) the forward run that computes J (1000 steps with
-    a Nu sample each, then lb_nusselt), all from lb_init's state."""
+    """The discrete adjoint on the 64^3 boiling cell (FP64, 1000 steps): wall time of
+    lb_adjoint_step (J and dJ/d(T_d, T_u, G)) with the segment length taken from free device
+    memory (every state's fields kept: 42 GB here) and with checkpoints every 50 steps, against
+    (a) the plain forward run, lb_step(1000) with no Nu sampling, and (b) the forward run that
+    computes J (1000 steps with a Nu sample each, then lb_nusselt), all from lb_init's state."""
     from paper_1111_0905_gb300 import config
     w = config.boiling_cell(64, kappa=0.15, tau_nu=1.25)
     p = w.params
@@ -499,7 +558,11 @@ def adjoint_cost(lb, torch) -> dict:
     lat.step(5)                    # warm-up of the kernels, then a fresh context for each run
     lat.close()
     lat = lb.Lattice(p, rho, T)
-    t_adj, got = wall(lambda: lat.adjoint(N, K))
+    t_adj, got = wall(lambda: lat.adjoint(N, 0))
+    lat.close()
+    torch.cuda.empty_cache()
+    lat = lb.Lattice(p, rho, T)
+    t_adj_k, got_k = wall(lambda: lat.adjoint(N, K))
     lat.close()
     lat = lb.Lattice(p, rho, T)
     t_plain, _ = wall(lambda: lat.step(N))
@@ -508,9 +571,14 @@ def adjoint_cost(lb, torch) -> dict:
     lat = lb.Lattice(q, rho, T)
     t_fwd, J = wall(lambda: (lat.step(N), lat.nusselt()[2])[1])
     lat.close()
-    return {"workload": "boiling cell 64^3 FP64, 1000 steps, checkpoints every 50",
-            "adjoint_s": t_adj, "forward_plain_s": t_plain, "forward_with_J_s": t_fwd,
+    return {"workload": "boiling cell 64^3 FP64, 1000 steps",
+            "adjoint_s": t_adj, "segment": "from free memory (checkpoint_every = 0): all 1000 states' fields",
+            "forward_plain_s": t_plain, "forward_with_J_s": t_fwd,
             "ratio_vs_plain_step": t_adj / t_plain, "ratio_vs_forward_with_J": t_adj / t_fwd,
+            "checkpointed_every_50": {"adjoint_s": t_adj_k, "ratio_vs_plain_step": t_adj_k / t_plain,
+                                      "ratio_vs_forward_with_J": t_adj_k / t_fwd,
+                                      "grad_rel_diff": max(abs(got_k[k] - got[k]) / abs(got[k])
+                                                           for k in ("T_d", "T_u", "G"))},
             "J": got["J"], "J_rel_diff_vs_forward": abs(got["J"] - J) / abs(J),
             "dJ_dTd": got["T_d"], "dJ_dTu": got["T_u"], "dJ_dG": got["G"]}
 

@@ -152,9 +152,12 @@ int lb_nusselt(lb_ctx* ctx, double* nu_mean, double* nu_z, double* nu_time_avg);
  * (kappa (T_d - T_u) nx ny) (the conduction term telescopes). Output pointers may be NULL.
  * Device memory: nsteps/checkpoint_every + 1 population checkpoints, checkpoint_every + 1 sets of
  * 20 float64 fields, 3 float64 states and 15 float64 fields, allocated and freed by the call.
- * Synchronises. Errors: LB_EINVAL (nsteps < 1, checkpoint_every < 1, T_d == T_u, dJ_dT0 requested
+ * checkpoint_every = 0 takes the longest segment whose buffers fit in 85 % of the device's free
+ * memory: all nsteps states' fields when they fit (with FP64 storage nothing is then recomputed),
+ * else the largest length that fits.
+ * Synchronises. Errors: LB_EINVAL (nsteps < 1, checkpoint_every < 0, T_d == T_u, dJ_dT0 requested
  * after lb_step), LB_EUNSUP (a scheme variant: the reverse pass transposes the paper's scheme
- * only), LB_ENOMEM, LB_ECUDA. */
+ * only), LB_ENOMEM (also: no segment length fits), LB_ECUDA. */
 int lb_adjoint_step(lb_ctx* ctx, long long nsteps, int checkpoint_every, double* J,
                     double* dJ_dTd, double* dJ_dTu, double* dJ_dG, double* dJ_dT0);
 
@@ -269,6 +272,26 @@ const char* lb_last_error(const lb_ctx* ctx);
 int lb_nusselt_fields_noalloc(const double* rho, const double* uz, const double* T,
                               int nx, int ny, int nz, double kappa, double G, double c_v,
                               double T_d, double T_u, double* nu_out, void* cuda_stream);
+
+/* lb_stream_bound -- a measurement aid, not a physical step: the memory access pattern of one
+ * time step (streaming of Eqs. (6)-(7): 19 f and 19 g pulled from the neighbours x - c_l, 19 + 19
+ * values written) with none of its arithmetic. For every node and direction l, f_out[l][node] =
+ * f_in[l][source] and g_out[l][node] = g_in[l][source], source = node - c_l, periodic in x and y,
+ * z clamped into [0, nz) (the step bounces back at the walls instead; the clamp keeps the same
+ * locality). Lattices [19][nz][ny][nx] in the library's direction order (0 rest, 1..6 axis +-x,
+ * +-y, +-z, 7..10 xy, 11..14 xz, 15..18 yz diagonals), elements of elem_bytes = 4 (float) or 2
+ * (any 16-bit type: bits are copied), device memory, caller-owned; the outputs must not overlap
+ * the inputs. Its bandwidth at the fused step's residency is the bound of the step's access
+ * pattern there.
+ * ctas_per_sm: 0 = one node per thread (256-thread CTAs covering the cell); k >= 1 = a single
+ * resident wave of SMs * k CTAs of 256 threads striding over the nodes (8k warps per SM).
+ * max_ctas_per_sm (may be NULL) receives the kernel's occupancy limit; a larger ctas_per_sm is
+ * refused. Enqueued on cuda_stream (NULL = legacy default stream) of the current device; nothing
+ * is synchronised.
+ * Errors: LB_EINVAL (null lattice pointer, nx/ny/nz < 1, 19 nx ny nz >= 2^32, elem_bytes not 2 or
+ * 4, ctas_per_sm < 0 or above the occupancy limit), LB_ECUDA (device query or launch failed). */
+int lb_stream_bound(int elem_bytes, const void* f_in, const void* g_in, void* f_out, void* g_out,
+                    int nx, int ny, int nz, int ctas_per_sm, int* max_ctas_per_sm, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ BUILD = PKG / "_build"
 LIB = PKG / "libthermal_lbm.so"
 SOURCES = ["lb_api.cu", "lb_prec_f64.cu", "lb_prec_f32.cu", "lb_prec_bf16.cu", "lb_prec_f16.cu",
            "lb_prec_f16loc.cu",
-           "lb_noalloc.cu", "lb_adjoint.cu", "lb_analysis.cu"]
+           "lb_noalloc.cu", "lb_adjoint.cu", "lb_analysis.cu", "lb_bound.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -14,6 +14,7 @@
 // macroscopic fields of a state are recomputed per reverse step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -378,17 +379,37 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
                                double* dJ_dTd, double* dJ_dTu, double* dJ_dG, double* dJ_dT0) {
   using namespace tlbm::adj;
   if (!c) return LB_EINVAL;
-  if (nsteps < 1 || checkpoint_every < 1) return lb_fail(c, LB_EINVAL, "nsteps and checkpoint_every must be >= 1");
+  if (nsteps < 1 || checkpoint_every < 0) return lb_fail(c, LB_EINVAL, "nsteps must be >= 1 and checkpoint_every >= 0");
   if (dJ_dT0 && (c->step != 0 || !c->from_init))
     return lb_fail(c, LB_EINVAL, "dJ_dT0 needs the state of lb_init (step 0)");
   if (!(c->p.T_d != c->p.T_u)) return lb_fail(c, LB_EINVAL, "T_d == T_u: Nu is undefined");
   if (c->p.forcing != FORCE_SHIFT || c->p.psi_kind != PSI_EXP)
     return lb_fail(c, LB_EUNSUP, "the adjoint transposes the paper's scheme (velocity shift, psi = exp(-1/rho)) only");
-  const long long K = checkpoint_every < nsteps ? checkpoint_every : nsteps;
-  const long long nck = (nsteps + K - 1) / K;
   const size_t N = (size_t)c->N;
   const size_t pbytes = (size_t)c->ops->slots * N * c->ops->esize;
   const size_t sbytes = 2 * (size_t)Q * N * sizeof(double);
+  const size_t mstate = (size_t)MF_COUNT * N;   // doubles per state's fields
+  // device bytes of the call for segment length k (the allocations below)
+  auto bytes_for = [&](long long k) -> double {
+    const double nck_k = (double)((nsteps + k - 1) / k);
+    return nck_k * 2.0 * (double)pbytes + 4.0 * (double)pbytes + 64.0 + 3.0 * (double)sbytes +
+           (double)(k + 1) * (double)mstate * 8.0 + (double)AF_COUNT * (double)N * 8.0 +
+           (double)kBlocks * P_COUNT * 8.0 + (dJ_dT0 ? (double)N * 8.0 : 0.0);
+  };
+  long long K = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+  if (checkpoint_every == 0) {
+    // the longest segment whose buffers fit in 85 % of the free device memory: every state's
+    // fields kept (no recomputation with FP64 storage) when they fit
+    size_t free_b = 0, total_b = 0;
+    LB_CU(c, cudaMemGetInfo(&free_b, &total_b));
+    const double budget = 0.85 * (double)free_b;
+    const double per_k = (double)mstate * 8.0;
+    long long k = std::min<long long>(nsteps, (long long)std::max(1.0, budget / per_k));
+    while (k > 1 && bytes_for(k) > budget) --k;
+    if (bytes_for(k) > budget) return lb_fail(c, LB_ENOMEM, "adjoint buffers do not fit for any segment length");
+    K = k;
+  }
+  const long long nck = (nsteps + K - 1) / K;
   cudaStream_t st = c->stream;
   Geom g{c->p.nx, c->p.ny, c->p.nz, c->plane, c->N};
 
@@ -396,7 +417,6 @@ extern "C" int lb_adjoint_step(lb_ctx* c, long long nsteps, int checkpoint_every
   // needs no separate moments, force and divergence passes; other storage recomputes them in
   // FP64 from the FP64 image of each state.
   const bool fields = (c->ops->esize == sizeof(double));
-  const size_t mstate = (size_t)MF_COUNT * N;   // doubles per state's fields
   DevBuf ck, rb, xs, mb, ab, lb, pt, d0;
   if (cudaMalloc(&ck.p, (size_t)nck * 2 * pbytes) != cudaSuccess ||
       cudaMalloc(&rb.p, 4 * pbytes + 64) != cudaSuccess ||

@@ -30,7 +30,8 @@ _lib = None
 EXPORTS = ("lb_init", "lb_step", "lb_adjoint_step", "lb_profiles", "lb_histogram_T_rho",
            "lb_structure_functions", "lb_moments", "lb_nusselt", "lb_populations", "lb_diagnostics",
            "lb_save", "lb_load", "lb_step_count", "lb_free", "lb_strerror", "lb_last_error",
-           "lb_nusselt_fields_noalloc", "lb_launch_info", "lb_heat_flux_pdf", "lb_set_populations")
+           "lb_nusselt_fields_noalloc", "lb_launch_info", "lb_heat_flux_pdf", "lb_set_populations",
+           "lb_stream_bound")
 NOALLOC_MAX_NZ = 8192
 
 
@@ -143,6 +144,8 @@ def load_library():
     lib.lb_launch_info.restype = I
     lib.lb_heat_flux_pdf.argtypes = [P, I, I, I, D, D, P, P]
     lib.lb_heat_flux_pdf.restype = I
+    lib.lb_stream_bound.argtypes = [I, P, P, P, P, I, I, I, I, ctypes.POINTER(I), P]
+    lib.lb_stream_bound.restype = I
     _lib = lib
     return lib
 
@@ -208,6 +211,30 @@ def nusselt_fields_noalloc(params: Params, rho, uz, T, nu_out, stream=None) -> N
         raise LBError(rc, "lb_nusselt_fields_noalloc", lib.lb_strerror(rc).decode())
 
 
+def stream_bound(f_in, g_in, f_out, g_out, shape, ctas_per_sm: int = 0, stream=None) -> int:
+    """lb_stream_bound on four contiguous CUDA tensors of one 4- or 2-byte dtype and 19 * nx*ny*nz
+    elements each (shape = (nz, ny, nx)): the step's streaming loads and stores without its
+    arithmetic, a bandwidth yardstick. Enqueued on the current stream; returns the kernel's
+    occupancy limit in CTAs per SM."""
+    import torch
+    lib = load_library()
+    nz, ny, nx = shape
+    n = 19 * nx * ny * nz
+    ts = (f_in, g_in, f_out, g_out)
+    for t in ts:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("stream_bound takes contiguous CUDA tensors")
+        if t.dtype != f_in.dtype or t.element_size() not in (2, 4) or t.numel() != n:
+            raise ValueError(f"stream_bound: tensors of one 2- or 4-byte dtype with {n} elements each")
+    out = ctypes.c_int(0)
+    st = _current_stream() if stream is None else stream
+    rc = lib.lb_stream_bound(f_in.element_size(), *[_ptr(t) for t in ts], nx, ny, nz, int(ctas_per_sm),
+                             ctypes.byref(out), st)
+    if rc != 0:
+        raise LBError(rc, "lb_stream_bound", lib.lb_strerror(rc).decode())
+    return out.value
+
+
 class Lattice:
     """A context of the C ABI: lb_init on construction, lb_free on close()."""
 
@@ -265,7 +292,8 @@ class Lattice:
 
     def adjoint(self, nsteps: int, checkpoint_every: int = 50, grad_T0: bool = False) -> dict:
         """lb_adjoint_step: J = time-averaged Nu over the next nsteps steps and dJ/d(T_d, T_u, G)
-        (and dJ/dT0 as [nz, ny, nx] if grad_T0; requires step 0)."""
+        (and dJ/dT0 as [nz, ny, nx] if grad_T0; requires step 0). checkpoint_every = 0: the longest
+        segment that fits in free device memory (every state's fields when they fit)."""
         J, dTd, dTu, dG = (ctypes.c_double() for _ in range(4))
         dT0 = np.empty(self.shape, dtype=np.float64) if grad_T0 else None
         self._check(self.lib.lb_adjoint_step(self.ctx, int(nsteps), int(checkpoint_every),

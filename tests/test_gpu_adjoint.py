@@ -217,3 +217,25 @@ def test_adjoint_of_the_16bit_forms_against_fp64(lblib, cuda, prec, tol):
     errs = {k: abs(g16[k] - g64[k]) / max(abs(g64[k]), 1e-3) for k in ("J", "T_d", "T_u", "G")}
     print("16-bit adjoint", prec, errs)
     assert max(errs.values()) <= tol, errs
+
+
+@pytest.mark.parametrize("prec", [lb.LB_FP64, lb.LB_FP32])
+def test_adjoint_segment_length_from_free_memory(lblib, cuda, prec):
+    """checkpoint_every = 0 keeps every state's fields when they fit (they do for 100 steps of the
+    24^3 cell): the same J and gradients as checkpoint_every = nsteps, bit for bit, and as the
+    checkpointed run with segments of 25 steps to rounding; a negative length is refused."""
+    w = config.boiling_cell(24)
+    rho, T = w.fields()
+    q = lb.Params(**{**w.params.__dict__, "precision": prec})
+    auto = lb.Lattice(q, rho, T).adjoint(100, 0, grad_T0=True)
+    full = lb.Lattice(q, rho, T).adjoint(100, 100, grad_T0=True)
+    seg = lb.Lattice(q, rho, T).adjoint(100, 25, grad_T0=True)
+    for k in ("J", "T_d", "T_u", "G"):
+        assert auto[k] == full[k], (k, auto[k], full[k])
+        assert abs(auto[k] - seg[k]) <= 1e-12 * max(abs(seg[k]), 1e-3), (k, auto[k], seg[k])
+    assert np.array_equal(auto["T0"], full["T0"])
+    lat = lb.Lattice(q, rho, T)
+    with pytest.raises(lb.LBError) as e:
+        lat.adjoint(10, -1)
+    assert e.value.code == -1
+    lat.close()

@@ -174,3 +174,21 @@ def test_boiling_block_equals_the_same_block_of_the_full_cell():
         b, Tb = synthetic.boiling_block(20, 12, 9, x0, y0, z0, sx, sy, sz, 1.5, 0.35, 0.31)
         assert np.array_equal(b, r[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx])
         assert np.array_equal(Tb, T[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx])
+
+
+def test_stream_bound_rejects_invalid_arguments_without_a_gpu(lblib):
+    """lb_stream_bound checks its arguments before any device call: null lattices, element sizes
+    other than 2 and 4, empty grids, 19 N offsets beyond 32 bits, a negative CTA count; the binding
+    refuses host tensors."""
+    import ctypes
+    import torch
+    fake = ctypes.c_void_p(256)
+    ok = (4, fake, fake, fake, fake, 8, 8, 8, 1, None, None)
+    for i, bad in [(0, 3), (0, 8), (1, None), (4, None), (5, 0), (7, -1), (8, -1)]:
+        args = list(ok)
+        args[i] = bad
+        assert lblib.lb_stream_bound(*args) == -1, (i, bad)
+    assert lblib.lb_stream_bound(4, fake, fake, fake, fake, 1024, 1024, 1024, 0, None, None) == -1
+    host = torch.zeros(19 * 8, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        lb.stream_bound(host, host, host, host, (2, 2, 2))
