@@ -422,6 +422,7 @@ def run_ours(args):
                "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_summary,
                "forms": results, "c5_1000_steps": c5, "sizes": sizes, "variants": variants,
                "diagnostics": diagnostics, "adjoint": adjoint, "horizon_errors": horizons,
+               "pattern_bound_sweep": pattern,
                "kernel_src_hash": src_hash}
         print(json.dumps(out))
     if ws > 1:
