@@ -336,9 +336,15 @@ template <int BY> struct Geo {
   template <class S> static constexpr size_t r_count() {
     return (size_t)(depth<S>() * (RXY + 5 * HXY) + 9 * HXY + 2 * fslots<S>() * TXY);
   }
+  // local-reference storage: the g references of the collision's sources, a radius-1 window of
+  // the tile in 4 planes, one 4-byte word (b1, b2) per node (tiles of 8 rows and more: at 4 rows
+  // the window's registers would spill)
+  template <class S> static constexpr bool gwin() { return IsLoc<S>::v && BY >= 8; }
+  template <class S> static constexpr size_t gwin_bytes() { return gwin<S>() ? sizeof(uint32_t) * 4 * HXY : 0; }
   template <class S, class R, bool STG> static constexpr size_t smem_bytes() {
     return sizeof(R) * r_count<S>() +
-           (STG ? sizeof(uint32_t) * (size_t)(2 * Q * TXY) : sizeof(S) * (size_t)(depth<S>() * Q * TXY));
+           (STG ? sizeof(uint32_t) * (size_t)(2 * Q * TXY) : sizeof(S) * (size_t)(depth<S>() * Q * TXY)) +
+           gwin_bytes<S>();
   }
 };
 
@@ -459,6 +465,24 @@ __device__ __forceinline__ void pull_raw_ref(float (&r)[Q], const S* __restrict_
   }
 }
 
+// The references of the 19 pulled g of node cw (index in the radius-1 window) from the window
+// of 4-byte words (b1 low, b2 high half) of planes z-1..z+1; across a wall (only when WALL) the
+// node's own word (bounce-back source). Same values as pull_raw_ref on the g lattice.
+template <bool WALL>
+__device__ __forceinline__ void win_ref(float (&r)[Q], const uint32_t* __restrict__ win, int z, int nz, int cw,
+                                        int hx, int hxy) {
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const int cz = CZ(l);
+    const bool through = WALL && ((cz > 0 && z == 0) || (cz < 0 && z == nz - 1));
+    const uint32_t w = through ? win[ring<4>(z) * hxy + cw]
+                               : win[ring<4>(z - cz) * hxy + cw - CY(l) * hx - CX(l)];
+    const float b1 = __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+    const float b2 = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+    r[l] = l == 0 ? 12.0f * (b1 - b2) : (CSQ(l) == 1 ? b1 : b2);
+  }
+}
+
 // The two stored references of a node (rounded to the storage format) from its moment deviations:
 // f: a1 = w1 drho, a2 = w2 (4.5 dE - 0.5 drho); g: b1 = w1 dE, b2 = w2 (4.5 lam dT - 0.5 dE).
 template <class S>
@@ -558,6 +582,9 @@ lb_fused_kernel(const KArgs a) {
   // the f cache (measured faster for them) and pull g directly.
   S* fc_s = reinterpret_cast<S*>(F_s + 2 * NFS * TXY);                 // [D][Q][TXY] (not STG)
   uint32_t* stg_s = reinterpret_cast<uint32_t*>(F_s + 2 * NFS * TXY);  // [2][Q][TXY] (STG)
+  constexpr bool GWIN = GE::template gwin<S>();
+  uint32_t* gw_s = reinterpret_cast<uint32_t*>(fc_s + D * Q * TXY);   // [4][HXY] g references (GWIN)
+  constexpr int NGW = (HXY + NT - 1) / NT;                               // window nodes per thread
 
   const S* __restrict__ fin = static_cast<const S*>(a.fin);
   const S* __restrict__ gin = static_cast<const S*>(a.gin);
@@ -615,6 +642,28 @@ lb_fused_kernel(const KArgs a) {
     const int z = p - 2;            // plane collided by this iteration's C stage
     const bool cplane = (z >= z0 && z < z1);
     const bool wallz = (z == 0 || z == nz - 1);
+    // local-reference storage: load the g references (b1, b2) of plane p-1 on the radius-1 window
+    // now; they are stored to the window behind the M stage (the collisions of planes p-2..p pull
+    // from it). Slot ring<4>(p-1) was last read by the collision of plane p-5, which every warp
+    // finished before the previous iteration's barrier.
+    unsigned short gwv[GWIN ? 2 * NGW : 1];
+    const int gq = p - 1;
+    const bool gload = GWIN && gq >= 0 && gq < nz && gq >= z0 - 1 && gq <= z1;
+    if constexpr (GWIN) {
+      if (gload) {
+        const unsigned short* gb = reinterpret_cast<const unsigned short*>(gin);
+#pragma unroll
+        for (int i = 0; i < NGW; ++i) {
+          const int k = tid + i * NT;
+          if (k < HXY) {
+            const int gx = wrapi(x0 + k % HX - 1, nx), gy = wrapi(y0 + k / HX - 1, ny);
+            const unsigned e = (unsigned)gq * plane + (unsigned)(gy * nx + gx);
+            gwv[2 * i] = __ldg(gb + e + (unsigned)Q * N);
+            gwv[2 * i + 1] = __ldg(gb + e + (unsigned)(Q + 1) * N);
+          }
+        }
+      }
+    }
     if constexpr (STG) {
       // start the copies of the collision's pulled f and g; they complete behind M and U
       if (cplane && cvalid) {
@@ -696,6 +745,16 @@ lb_fused_kernel(const KArgs a) {
         }
       }
     }
+    if constexpr (GWIN) {
+      if (gload) {
+        uint32_t* w = gw_s + ring<4>(gq) * HXY;
+#pragma unroll
+        for (int i = 0; i < NGW; ++i) {
+          const int k = tid + i * NT;
+          if (k < HXY) w[k] = (uint32_t)gwv[2 * i] | ((uint32_t)gwv[2 * i + 1] << 16);
+        }
+      }
+    }
     __syncthreads();
     if constexpr (DIAG) {
       // the partials of the plane collided in the previous iteration are complete
@@ -770,14 +829,17 @@ lb_fused_kernel(const KArgs a) {
 #pragma unroll
         for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fc[l * TXY]);
         if constexpr (IsLoc<S>::v) {
-          // the references of the sources: f's and g's at the same slots of their lattices
+          // the references of the sources: f's from its lattice, g's from the window (GWIN)
           float rf[Q], rg[Q];
+          const int cw = (ty + 1) * HX + (tx + 1);
           if (wallz) {
             pull_raw_ref<S, true>(rf, fin, N, z, nz, plane, ccol, crow);
-            pull_raw_ref<S, true>(rg, gin, N, z, nz, plane, ccol, crow);
+            if constexpr (GWIN) win_ref<true>(rg, gw_s, z, nz, cw, HX, HXY);
+            else pull_raw_ref<S, true>(rg, gin, N, z, nz, plane, ccol, crow);
           } else {
             pull_raw_ref<S, false>(rf, fin, N, z, nz, plane, ccol, crow);
-            pull_raw_ref<S, false>(rg, gin, N, z, nz, plane, ccol, crow);
+            if constexpr (GWIN) win_ref<false>(rg, gw_s, z, nz, cw, HX, HXY);
+            else pull_raw_ref<S, false>(rg, gin, N, z, nz, plane, ccol, crow);
           }
 #pragma unroll
           for (int l = 0; l < Q; ++l) { f[l] = f[l] + rf[l]; g[l] = g[l] + rg[l]; }
