@@ -140,6 +140,7 @@ KArgs make_args(const lb_ctx* c) {
   std::memset(&a, 0, sizeof(a));
   a.fin = c->f[c->cur]; a.gin = c->g[c->cur];
   a.fout = c->f[1 - c->cur]; a.gout = c->g[1 - c->cur];
+  a.pre = c->pre;
   a.nx = c->p.nx; a.ny = c->p.ny; a.nz = c->p.nz; a.plane = c->plane; a.N = c->N;
   a.tiles_x = c->tiles_x; a.ntiles = c->ntiles; a.zc = c->zc;
   a.forcing = c->p.forcing; a.psi_kind = c->p.psi_kind;
@@ -176,7 +177,7 @@ void free_all(lb_ctx* c) {
   if (!c) return;
   for (int k = 0; k < 2; ++k) { cudaFree(c->f[k]); cudaFree(c->g[k]); }
   cudaFree(c->part); cudaFree(c->diag); cudaFree(c->nu_acc);
-  cudaFree(c->fields); cudaFree(c->pops);
+  cudaFree(c->fields); cudaFree(c->pops); cudaFree(c->pre);
 }
 
 }  // namespace
@@ -367,6 +368,11 @@ int lb_init(const lb_params* params, const double* rho_init, const double* T_ini
       cudaFree(staging);
       return bail(LB_ENOMEM);
     }
+  }
+  // FP64: per-node moments and psi that each step kernel's ring reads (lb_fields_kernel)
+  if (ops->esize == sizeof(double) && cudaMalloc(&c->pre, 6 * (size_t)N * sizeof(double)) != cudaSuccess) {
+    cudaFree(staging);
+    return bail(LB_ENOMEM);
   }
   if (cudaMalloc(&c->part, (size_t)p.nz * c->ntiles * NPART * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->diag, (size_t)(8 * p.nz + 8) * sizeof(double)) != cudaSuccess ||

@@ -23,6 +23,7 @@ struct lb_ctx {
   double* nu_acc = nullptr;  // [2]
   double* fields = nullptr;  // [5][N] staging for host-bound lb_moments
   double* pops = nullptr;    // [38][N] staging for host-bound lb_populations
+  double* pre = nullptr;     // FP64 form: [6][N] rho, 1/rho, j, psi of the state a step reads
   long long step = 0;
   // the current state is due for a Nu sample (nu_every) that the next step's launch takes in
   // passing (fused step + diagnostics); lb_nusselt, lb_diagnostics, lb_save and

@@ -154,6 +154,7 @@ struct KArgs {
   double* rho_out; double* ux_out; double* uy_out; double* uz_out; double* T_out;
   double* part;                       // [nz][ntiles][NPART] diagnostics partials (may be null)
   double* adj_m;                      // FP64 step: MF_* fields of the state read ([MF_COUNT][N]) or null
+  double* pre;                        // FP64 form: rho, 1/rho, jx, jy, jz, psi of the state read ([6][N])
   KPar<double> pd;                    // the parameters above in double ...
   KPar<float> pf;                     // ... and in float
 };
@@ -340,10 +341,14 @@ template <int BY> struct Geo {
   // the tile in 4 planes, one 4-byte word (b1, b2) per node (tiles of 8 rows and more: at 4 rows
   // the window's registers would spill)
   template <class S> static constexpr bool gwin() { return IsLoc<S>::v && BY >= 8; }
+  // the f cache of the tile's pulled populations (16-bit forms); FP64 takes its ring's moments and
+  // psi from the per-node pre-pass and pulls the collision's f directly
+  template <class S> static constexpr bool fcache() { return !std::is_same<S, double>::value; }
   template <class S> static constexpr size_t gwin_bytes() { return gwin<S>() ? sizeof(uint32_t) * 4 * HXY : 0; }
   template <class S, class R, bool STG> static constexpr size_t smem_bytes() {
     return sizeof(R) * r_count<S>() +
-           (STG ? sizeof(uint32_t) * (size_t)(2 * Q * TXY) : sizeof(S) * (size_t)(depth<S>() * Q * TXY)) +
+           (STG ? sizeof(uint32_t) * (size_t)(2 * Q * TXY)
+                : (fcache<S>() ? sizeof(S) * (size_t)(depth<S>() * Q * TXY) : 0)) +
            gwin_bytes<S>();
   }
 };
@@ -548,7 +553,7 @@ __device__ __forceinline__ void moments_combine(const KArgs& a, int z, int tile,
 }
 
 template <class S, int BY> struct MinBlocks { static constexpr int v = 512 / (BX * BY) > 0 ? 512 / (BX * BY) : 1; };
-template <int BY> struct MinBlocks<double, BY> { static constexpr int v = 1; };
+template <int BY> struct MinBlocks<double, BY> { static constexpr int v = 2; };
 
 template <class S, int BY, int MODE, int VAR = 0>
 __global__ void __launch_bounds__(BX * BY, MinBlocks<S, BY>::v)
@@ -573,6 +578,7 @@ lb_fused_kernel(const KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool STG = std::is_same<S, float>::value && TLBM_STAGE;
   constexpr int D = GE::template depth<S>();
+  constexpr bool PRE = std::is_same<S, double>::value;   // FP64: ring fields from lb_fields_kernel
   R* psi_s = reinterpret_cast<R*>(smem_raw);  // [D][RXY]
   R* rj_s = psi_s + D * RXY;                  // [D][5][HXY]  rho, 1/rho, jx, jy, jz
   R* u_s = rj_s + D * 5 * HXY;                // [3][3][HXY]  physical velocity
@@ -707,6 +713,19 @@ lb_fused_kernel(const KArgs a) {
 #pragma unroll
       for (int i = 0; i < MAXM; ++i) {
         const int k = tid + i * NT;
+        if constexpr (PRE) {
+          // FP64: the ring node's moments and psi from the per-node pre-pass
+          if (k < RXY) {
+            const double* pr = a.pre + (zb + (unsigned)mown[i]);
+            psi_s[s3 * RXY + k] = pr[5 * (size_t)N];
+            if (mh[i] >= 0) {
+              R* rj = rj_s + s3 * 5 * HXY + mh[i];
+              rj[0] = pr[0]; rj[HXY] = pr[(size_t)N]; rj[2 * HXY] = pr[2 * (size_t)N];
+              rj[3 * HXY] = pr[3 * (size_t)N]; rj[4 * HXY] = pr[4 * (size_t)N];
+            }
+          }
+          continue;
+        }
         if (k < RXY) {
           S fr[Q];
           if constexpr (REL) {
@@ -825,9 +844,18 @@ lb_fused_kernel(const KArgs a) {
         else pull_raw<S, false>(gr, gin, N, z, nz, plane, ccol, crow);
 #pragma unroll
         for (int l = 0; l < Q; ++l) g[l] = cvt<S, R>(gr[l]);
-        const S* fc = fc_s + ring<D>(z) * Q * TXY + t;
+        if constexpr (PRE) {
+          // FP64 keeps no f cache: the collision pulls its f like its g
+          S fr[Q];
+          if (wallz) pull_raw<S, true>(fr, fin, N, z, nz, plane, ccol, crow);
+          else pull_raw<S, false>(fr, fin, N, z, nz, plane, ccol, crow);
 #pragma unroll
-        for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fc[l * TXY]);
+          for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fr[l]);
+        } else {
+          const S* fc = fc_s + ring<D>(z) * Q * TXY + t;
+#pragma unroll
+          for (int l = 0; l < Q; ++l) f[l] = cvt<S, R>(fc[l * TXY]);
+        }
         if constexpr (IsLoc<S>::v) {
           // the references of the sources: f's from its lattice, g's from the window (GWIN)
           float rf[Q], rg[Q];
@@ -1034,6 +1062,45 @@ lb_fused_kernel(const KArgs a) {
       moments_combine<R, BY>(a, z1 - 1, tile, tid);
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 form, before each step-kernel launch: rho, 1/rho, j (Eq. (8)) and psi of every node of the
+// state a.fin, once per node, into a.pre ([6][N]). On GB300 the FP64 step is bound by its FP64
+// instructions; its M stage would otherwise form these for the radius-2 ring of every tile, 1.69
+// times per node. Same pulls (with the walls' bounce-back sources) and the same operations in the
+// same order as the M stage, so the step's results are unchanged bit for bit. One node per thread.
+// ---------------------------------------------------------------------------------------
+template <bool VDW>
+__global__ void __launch_bounds__(256) lb_fields_kernel(const KArgs a) {
+  const double* __restrict__ fin = static_cast<const double*>(a.fin);
+  const unsigned N = (unsigned)a.N, plane = (unsigned)a.plane;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int x = (int)(idx % (unsigned)nx), y = (int)((idx / (unsigned)nx) % (unsigned)ny);
+  const int z = (int)(idx / plane);
+  int col[3], row[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    col[j] = wrapi(x - 1 + j, nx);
+    row[j] = wrapi(y - 1 + j, ny) * nx;
+  }
+  double f[Q];
+  if (z == 0 || z == nz - 1) pull_raw<double, true>(f, fin, N, z, nz, plane, col, row);
+  else pull_raw<double, false>(f, fin, N, z, nz, plane, col, row);
+  double drho, jx, jy, jz;
+  density_momentum<double>(f, drho, jx, jy, jz);
+  const KPar<double>& kp = a.pd;
+  const double rho = kp.rho0 + drho;
+  const double inv = rcp(rho);
+  double* o = a.pre + idx;
+  o[0] = rho;
+  o[(size_t)N] = inv;
+  o[2 * (size_t)N] = jx;
+  o[3 * (size_t)N] = jy;
+  o[4 * (size_t)N] = jz;
+  o[5 * (size_t)N] = VDW ? psi_vdw(rho, kp) : fexp(-inv);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -27,10 +27,13 @@ template <class S> struct OpsImpl {
   using R = typename Store<S>::R;
 
   // dynamic shared memory of a tile height; tile heights whose windows exceed the 227 KB a CTA
-  // may use are not available (FP64 with BY = 16)
+  // may use are not available, nor FP64 with BY = 16 (a CTA of 512 threads leaves the FP64
+  // collision 128 registers per thread, too few for its 38 double-precision populations)
   static constexpr bool STG = std::is_same<S, float>::value && TLBM_STAGE;
   template <int BY> static constexpr size_t smem() { return Geo<BY>::template smem_bytes<S, R, STG>(); }
-  template <int BY> static constexpr bool fits() { return smem<BY>() + 1024 <= 227u * 1024u; }
+  template <int BY> static constexpr bool fits() {
+    return smem<BY>() + 1024 <= 227u * 1024u && !(std::is_same<S, double>::value && BY > 8);
+  }
   template <int BY, int MODE, int VAR = 0> static cudaError_t attr() {
     if constexpr (!fits<BY>()) {
       return cudaSuccess;
@@ -112,6 +115,15 @@ template <class S> struct OpsImpl {
     return go<BY, MODE_MOMENTS, 0>(a, grid, st);
   }
   static cudaError_t fused(const KArgs& a, int mode, int by, dim3 grid, cudaStream_t st) {
+    if constexpr (std::is_same<S, double>::value) {
+      // FP64: the ring's moments and psi of the state read, once per node, before the step
+      if (a.pre == nullptr) return cudaErrorInvalidValue;
+      const unsigned blocks = ((unsigned)a.N + 255u) / 256u;
+      if (a.psi_kind == PSI_VDW) lb_fields_kernel<true><<<blocks, 256, 0, st>>>(a);
+      else lb_fields_kernel<false><<<blocks, 256, 0, st>>>(a);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
     if (by == 4) return go_by<4>(a, mode, grid, st);
     if (by == 8) return go_by<8>(a, mode, grid, st);
     if (by == 16) return go_by<16>(a, mode, grid, st);
