@@ -50,18 +50,18 @@ KERNEL_TYPE = {"f64": "double", "f32": "float", "bf16dev": "__nv_bfloat16", "fp1
 # launch time is kept to a few GB on the device), keyed by the hash of the kernel sources it
 # was taken on. The headline's traffic is that capture scaled by the node count (the traffic
 # of one launch grows in proportion to the nodes it updates); null once the sources changed.
-TRAFFIC = {"src_hash": "d565c1fa97fe78bb", "nodes": 192 ** 3,
-           "bytes_per_launch": {"f32": 1146717184 + 1031767296, "fp16loc": 601976832 + 553474560,
-                                "fp16dev": 543572480 + 495248640},
+TRAFFIC = {"src_hash": "89f84465a4989b8a", "nodes": 192 ** 3,
+           "bytes_per_launch": {"f32": 1148334592 + 1032008960, "fp16loc": 602396672 + 553547520,
+                                "fp16dev": 543652608 + 495205632},
            "what": "ncu DRAM bytes of one launch of the 192^3 paper-geometry cell, scaled by the node count"}
 
-# FP64 operations per node of the FP64 step kernel (ncu: 2 x DFMA + DADD + DMUL thread
-# instructions of one launch of the 128^3 single-phase cell, 2 x 395,800,576 + 241,686,528 +
-# 116,529,152, divided by its 2,097,152 nodes; this counts the ring recomputation, i.e. the work
-# the kernel issues, and slightly overstates 512^3, whose chunk prologues are a smaller share),
-# and GB300's nominal FP64 rate (152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz = 1.26
-# TFLOP/s; no measured FP64 peak).
-FP64_FLOPS_PER_NODE = (2 * 395800576 + 241686528 + 116529152) / 2097152
+# FP64 operations per node of one FP64 step (ncu: 2 x DFMA + DADD + DMUL thread instructions of
+# one step of the 128^3 single-phase cell, i.e. the per-node pre-pass lb_fields_kernel,
+# 2 x 39,845,888 + 100,663,296, plus the step kernel, 2 x 327,282,688 + 91,111,424 + 129,517,568,
+# divided by its 2,097,152 nodes; the step kernel's count includes its chunk prologues, a smaller
+# share at 512^3), and GB300's nominal FP64 rate (152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07
+# GHz = 1.26 TFLOP/s; no measured FP64 peak).
+FP64_FLOPS_PER_NODE = (2 * (39845888 + 327282688) + (100663296 + 91111424) + 129517568) / 2097152
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
